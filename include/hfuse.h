@@ -1,0 +1,288 @@
+/*
+ * hfuse.h -- C ABI of the GB300 horizontal-fusion runtime.
+ *
+ * Horizontal fusion (Sec. 1.1, Sec. 2.2 of "Automatic Horizontal Fusion for
+ * GPU Kernels", Li, Zheng, Pekhimenko, Long, arXiv 2007.01277) runs two or
+ * more independent kernels as ONE launch: each thread block of d0 threads is
+ * cut into warp-aligned thread intervals, a thread-index branch sends every
+ * interval to one original kernel's body (Algorithm 1, Sec. 3.1), each body's
+ * block barrier becomes a named barrier "bar.sync id, d_k" over its own
+ * interval only, and the fused kernel's shared memory is the sum of the
+ * bodies' (Sec. 2.3).  The thread split and a register bound are chosen by
+ * profiling (Algorithm 2, Sec. 3.2).
+ *
+ * This library does not rewrite CUDA source.  Its kernels are hand-written
+ * "bodies" that already address threads through an interval context, so one
+ * body serves a standalone launch and any fused interval.  A fused instance
+ * is a compiled kernel per (body A, body B, register cap); split, block
+ * size, grid and barrier ids are launch-time values.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* or held in argument blocks are DEVICE pointers the
+ *     caller allocates and owns; the library never frees them.  Handles
+ *     (hf_kernel, hf_fused) are owned by the library until destroyed.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy stream).
+ *     Launches are asynchronous; argument blocks are copied at launch, so
+ *     the caller may reuse them as soon as the call returns.
+ *   - Every function returns an hf_status; no exception or abort crosses the
+ *     boundary.  On error nothing is launched and hf_last_error() gives a
+ *     one-line reason.  All validation happens on the host before a launch.
+ *   - One device: the device current on the calling thread when a handle is
+ *     created is the device it launches on.
+ */
+#ifndef HFUSE_H
+#define HFUSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HF_ABI_VERSION 1
+#define HF_MAX_INTERVALS 15   /* named barrier ids 1..15; id 0 stays the block barrier */
+#define HF_MAX_SCHEDULE 16    /* kernels per N-way fused launch                     */
+#define HF_POLY_NCOEF 33      /* degree-32 polynomial                                */
+
+typedef enum {
+    HF_OK = 0,
+    HF_ERR_INVALID = -1,      /* bad argument, null pointer, bad size or alignment  */
+    HF_ERR_SPLIT = -2,        /* thread split not warp aligned / out of range       */
+    HF_ERR_BARRIER = -3,      /* more intervals with barriers than named ids        */
+    HF_ERR_SMEM = -4,         /* combined shared memory above the per-block limit   */
+    HF_ERR_REGS = -5,         /* block too large for the instance's register use    */
+    HF_ERR_UNSUPPORTED = -6,  /* register cap or body combination not compiled      */
+    HF_ERR_CUDA = -7,         /* a CUDA runtime call failed (message has the name)  */
+    HF_ERR_TIMEOUT = -8       /* a bounded wait expired                             */
+} hf_status;
+
+/* Built-in constituent bodies. */
+typedef enum {
+    HF_BODY_BN_STATS = 0,     /* batch-norm mean / biased variance (Sec. 2.3)        */
+    HF_BODY_UPSAMPLE2X = 1,   /* bilinear x2, half-pixel centres (Sec. 4.1)          */
+    HF_BODY_MAXPOOL3S2 = 2,   /* 3x3 max pool, stride 2, pad 1 (Sec. 4.1)            */
+    HF_BODY_IM2COL3 = 3,      /* 3x3 im2col, stride 1, pad 1 (Sec. 4.1)              */
+    HF_BODY_HIST256 = 4,      /* 256-bin byte histogram, shared atomics (Sec. 2.3)   */
+    HF_BODY_PHILOX = 5,       /* Philox4x32-10 stream                                */
+    HF_BODY_POLY = 6,         /* repeated degree-32 Horner chain                     */
+    HF_BODY_BF16_AXPY = 7,    /* out = bf16(alpha*x + y)                             */
+    HF_BODY_STREAM_TMPL = 8,  /* parametric stream kernel (cost-model corpus)        */
+    HF_BODY_COUNT = 9
+} hf_body_id;
+
+/* ------------------------------------------------------------------ */
+/* Argument blocks, one per body.  All tensors are dense, row-major.   */
+
+/* Per-channel statistics of x[N][C][HW] (float32): mean[c] and the biased
+ * variance var[c] over the N*HW values of channel c.  `workspace` is
+ * device scratch of hf_workspace_size() bytes that must be zero-filled
+ * before its first use; every completed launch leaves it zero-filled again,
+ * so one workspace serves any number of launches on one stream (launches
+ * that overlap in time need separate workspaces).  Requires HW % 4 == 0 and
+ * x 16-byte aligned for the vector path; other shapes use a scalar path. */
+typedef struct {
+    const float *x;
+    float *mean;
+    float *var;
+    int N, C, HW;
+    void *workspace;
+} hf_bn_stats_args;
+
+/* y[P][2H][2W] = bilinear x2 upsampling of x[P][H][W], align_corners=false
+ * (source coordinate max(0, (o + 0.5)/2 - 0.5), clamped neighbours). */
+typedef struct {
+    const float *x;
+    float *y;
+    int P, H, W;
+} hf_upsample2x_args;
+
+/* y[P][Ho][Wo] = 3x3 max over the in-bounds window at (2*oy-1, 2*ox-1),
+ * Ho = (H-1)/2 + 1, Wo = (W-1)/2 + 1. */
+typedef struct {
+    const float *x;
+    float *y;
+    int P, H, W;
+} hf_maxpool3s2_args;
+
+/* col[n][c*9 + ky*3 + kx][oy*W + ox] = x[n][c][oy+ky-1][ox+kx-1] or 0. */
+typedef struct {
+    const float *x;
+    float *col;
+    int N, C, H, W;
+} hf_im2col3_args;
+
+/* bins[v] += number of bytes equal to v in x[0..n).  The body ADDS into
+ * bins (as the paper's histogram kernel does into a zeroed output): the
+ * caller zero-fills bins before the launch. */
+typedef struct {
+    const uint8_t *x;
+    uint32_t *bins;
+    int64_t n;
+} hf_hist256_args;
+
+/* out[i][0..3] = Philox4x32-10 block for counter (lo32(first+i),
+ * hi32(first+i), 0, 0) under key (lo32(seed), hi32(seed)), i < n. */
+typedef struct {
+    uint32_t *out;
+    int64_t n;
+    uint64_t seed;
+    uint64_t first;
+} hf_philox_args;
+
+/* y[i] = acc_iters(x[i]) with acc_0 = 0 and, per step,
+ * h = acc; for k = 32..0: h = fma(h, x, coef[k]); acc = h.
+ * Coefficients travel by value in the argument block. */
+typedef struct {
+    const float *x;
+    float *y;
+    int64_t n;
+    int iters;
+    float coef[HF_POLY_NCOEF];
+} hf_poly_args;
+
+/* out[i] = bf16_rne(alpha * x[i] + y[i]); x, y, out hold bfloat16 bits. */
+typedef struct {
+    const uint16_t *x;
+    const uint16_t *y;
+    uint16_t *out;
+    int64_t n;
+    float alpha;
+} hf_bf16_axpy_args;
+
+/* Parametric stream kernel: for each 16-byte group of x (n floats, n % 4 ==
+ * 0, 16-byte aligned) apply k multiply-adds v = v*a + b, the j-th to
+ * component j % 4, and store the group to y.  Each tile of the loop stages
+ * through `smem_bytes` of shared memory (0..49152, multiple of 16) and
+ * passes `n_barriers` (0..4) interval barriers; neither changes the values. */
+typedef struct {
+    const float *x;
+    float *y;
+    int64_t n;
+    int k;
+    int n_barriers;
+    int smem_bytes;
+    float a, b;
+} hf_stream_tmpl_args;
+
+/* ------------------------------------------------------------------ */
+/* Kernels and fused kernels.                                          */
+
+typedef struct hf_kernel_t *hf_kernel;
+typedef struct hf_fused_t *hf_fused;
+
+/* A registered kernel: one built-in body plus the interval sizes it may run
+ * with (the tunable block dimension of Sec. 2.1).  0 selects the default:
+ * min 32, max 1024, granularity 32.  Sizes must be multiples of 32. */
+typedef struct {
+    const char *name;
+    int body_id;
+    int min_threads;
+    int max_threads;
+    int thread_granularity;
+} hf_kernel_desc;
+
+/* Register a kernel.  HF_ERR_INVALID for an unknown body or sizes that are
+ * not multiples of 32 / not ordered. */
+hf_status hf_register_kernel(const hf_kernel_desc *desc, hf_kernel *out);
+void hf_destroy_kernel(hf_kernel k);
+
+/* Fuse two kernels (Algorithm 1, Sec. 3.1): a block of d0 threads whose
+ * threads [0, split) run kernel a with "bar.sync 1, split" and threads
+ * [split, d0) run kernel b with "bar.sync 2, d0 - split".  regcap = 0 for no
+ * register bound, else one of hf_regcaps().  Errors: HF_ERR_SPLIT when split
+ * is not a multiple of 32 with 0 < split < d0 <= 1024 or violates a kernel's
+ * thread range; HF_ERR_UNSUPPORTED for an uncompiled register cap. */
+hf_status hf_fuse(hf_kernel a, hf_kernel b, int split, int d0, int regcap,
+                  hf_fused *out);
+
+/* N-way fusion into one persistent kernel.  n kernels ks[0..n) are placed on
+ * n_intervals intervals of interval_threads[i] threads each (block size =
+ * their sum); kernel j runs on interval interval_of[j], and kernels sharing
+ * an interval run one after another in index order.  Interval i uses named
+ * barrier i + 1.  n <= HF_MAX_SCHEDULE, n_intervals <= HF_MAX_INTERVALS. */
+hf_status hf_fuse_n(const hf_kernel *ks, int n, const int *interval_of,
+                    const int *interval_threads, int n_intervals, int regcap,
+                    hf_fused *out);
+void hf_destroy_fused(hf_fused f);
+
+/* Launch a fused kernel: args[j] points to the argument block of kernel j
+ * (the type its body id names).  grid = number of blocks; 0 picks
+ * blocks_per_sm * SM count, where blocks_per_sm is the occupancy limit of
+ * the instance at this block size and shared memory.  The bodies stride over
+ * the grid, so any grid >= 1 computes the full result. */
+hf_status hf_launch(hf_fused f, const void *const *args, int grid, void *stream);
+
+/* Launch one kernel alone with `threads` threads per block (the unfused
+ * baseline, Sec. 4.1).  Same argument block as in a fused launch; a body run
+ * alone on d threads and grid g computes bit-identical results to the same
+ * body on a d-thread interval of a fused launch with grid g. */
+hf_status hf_launch_single(hf_kernel k, const void *args, int threads, int grid,
+                           void *stream);
+
+/* Resource use of a fused instance at its block size (Sec. 2.1, Sec. 4.3):
+ * registers per thread, spill bytes (local memory per thread), combined
+ * dynamic shared memory for `args`, and resident blocks per SM. */
+typedef struct {
+    int regs;
+    int spill_bytes;
+    int smem_bytes;
+    int block_threads;
+    int blocks_per_sm;
+    int max_threads_per_block;
+    int n_intervals;
+} hf_fused_info;
+
+hf_status hf_query(hf_fused f, const void *const *args, hf_fused_info *info);
+
+/* The same figures for a kernel launched alone with `threads` threads. */
+hf_status hf_query_single(hf_kernel k, const void *args, int threads,
+                          hf_fused_info *info);
+
+/* Scratch bytes a body needs for this argument block (0 for most bodies). */
+hf_status hf_workspace_size(int body_id, const void *args, size_t *bytes);
+
+/* The register caps that have compiled fused instances (ascending; the list
+ * excludes 0, which is always available).  Writes at most cap entries and
+ * returns the count. */
+int hf_regcaps(int *caps, int cap);
+
+/* Device limits used by the occupancy rule of Sec. 2.1 and the register
+ * bound of Algorithm 2: registers, shared memory and threads per SM, SM
+ * count, per-block opt-in shared memory and L2 bytes of the current device. */
+typedef struct {
+    int sm_count;
+    int regs_per_sm;
+    int smem_per_sm;
+    int threads_per_sm;
+    int smem_per_block_optin;
+    int l2_bytes;
+    int cc_major, cc_minor;
+} hf_device_limits;
+
+hf_status hf_device_info(hf_device_limits *lim);
+
+/* Register bound r0 of Algorithm 2 (Sec. 3.2) for a split d1 / d2 given the
+ * standalone kernels' registers per thread and the fused shared memory,
+ * using the limits in lim.  Writes 0 when the fused block cannot be
+ * resident.  Host arithmetic only. */
+hf_status hf_register_bound(const hf_device_limits *lim, int d1, int nregs1,
+                            int d2, int nregs2, int smem_fused, int *r0);
+
+/* Waits until all work queued on `stream` has finished, polling for at most
+ * timeout_ms milliseconds: HF_ERR_TIMEOUT if it has not finished by then
+ * (the work keeps running; nothing is cancelled), HF_ERR_CUDA if the stream
+ * reports an error.  The launch-timeout check of the failure-detection
+ * path; it never blocks longer than the limit. */
+hf_status hf_stream_wait(void *stream, int timeout_ms);
+
+const char *hf_status_string(hf_status s);
+/* One-line description of the most recent error on this thread. */
+const char *hf_last_error(void);
+/* Size of the argument block of a body (for binding checks). */
+size_t hf_args_size(int body_id);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HFUSE_H */

@@ -1,0 +1,208 @@
+// body_fp.cuh -- floating-point bodies: the FMA-chain polynomial, bf16
+// scale+add, and the parametric stream template used to generate the
+// cost-model corpus.
+#pragma once
+#include "hf_device.cuh"
+
+namespace hf {
+
+// ------------------------------------------------------------------------
+// Polynomial chain: acc <- acc * x^33 + p(x), evaluated as one 33-step
+// Horner pass per iteration, `iters` iterations.  Each thread runs four
+// independent elements (one 128-bit group) so every warp has four dependent
+// FMA chains in flight; the coefficients are read once into registers.
+struct BodyPoly {
+    using Args = hf_poly_args;
+    static constexpr int kId = HF_BODY_POLY;
+    static constexpr int kBarriers = 0;
+
+    static __host__ size_t workspace_bytes(const Args &) { return 0; }
+    static __host__ size_t smem_bytes(int, const Args &) { return 0; }
+    static __host__ hf_status validate(const Args &a)
+    {
+        if (a.n < 0 || a.iters < 0) return HF_ERR_INVALID;
+        if (a.n > 0 && (!a.x || !a.y)) return HF_ERR_INVALID;
+        return HF_OK;
+    }
+
+    template <int L>
+    static __device__ __forceinline__ void chain(float (&v)[L], const float (&c)[HF_POLY_NCOEF],
+                                                 int iters)
+    {
+        float acc[L], x[L];
+#pragma unroll
+        for (int l = 0; l < L; ++l) x[l] = v[l], acc[l] = 0.f;
+#pragma unroll 1
+        for (int t = 0; t < iters; ++t) {
+#pragma unroll
+            for (int k = HF_POLY_NCOEF - 1; k >= 0; --k)
+#pragma unroll
+                for (int l = 0; l < L; ++l) acc[l] = __fmaf_rn(acc[l], x[l], c[k]);
+        }
+#pragma unroll
+        for (int l = 0; l < L; ++l) v[l] = acc[l];
+    }
+
+    static __device__ void run(const Args &a, const Ctx &cx)
+    {
+        float c[HF_POLY_NCOEF];
+#pragma unroll
+        for (int k = 0; k < HF_POLY_NCOEF; ++k) c[k] = a.coef[k];
+        const int64_t gt = (int64_t)cx.block * cx.nthreads + cx.tid;
+        const int64_t stride = (int64_t)cx.grid * cx.nthreads;
+        int64_t done = 0;
+        if (aligned16(a.x) && aligned16(a.y)) {
+            const int64_t n4 = a.n >> 2;
+            for (int64_t i = gt; i < n4; i += stride) {
+                const float4 q = ldcs4(a.x + 4 * i);
+                float v[4] = {q.x, q.y, q.z, q.w};
+                chain<4>(v, c, a.iters);
+                stcs4(a.y + 4 * i, make_float4(v[0], v[1], v[2], v[3]));
+            }
+            done = n4 << 2;
+        }
+        for (int64_t i = done + gt; i < a.n; i += stride) {
+            float v[1] = {__ldg(a.x + i)};
+            chain<1>(v, c, a.iters);
+            a.y[i] = v[0];
+        }
+    }
+};
+
+// ------------------------------------------------------------------------
+// bf16 scale+add: out = bf16_rne(alpha * x + y), one FP32 fused multiply-add
+// then one rounding to bf16 (ties to even).  Eight elements per 128-bit
+// load.
+struct BodyBf16Axpy {
+    using Args = hf_bf16_axpy_args;
+    static constexpr int kId = HF_BODY_BF16_AXPY;
+    static constexpr int kBarriers = 0;
+
+    static __host__ size_t workspace_bytes(const Args &) { return 0; }
+    static __host__ size_t smem_bytes(int, const Args &) { return 0; }
+    static __host__ hf_status validate(const Args &a)
+    {
+        if (a.n < 0) return HF_ERR_INVALID;
+        if (a.n > 0 && (!a.x || !a.y || !a.out)) return HF_ERR_INVALID;
+        return HF_OK;
+    }
+
+    static __device__ __forceinline__ float lo(unsigned w) { return __uint_as_float(w << 16); }
+    static __device__ __forceinline__ float hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
+    static __device__ __forceinline__ unsigned pack(float u, float v)
+    {
+        __nv_bfloat162 h = __floats2bfloat162_rn(u, v);   // .x = u (low half)
+        return *reinterpret_cast<unsigned *>(&h);
+    }
+    static __device__ __forceinline__ unsigned axpy2(float al, unsigned x, unsigned y)
+    {
+        return pack(__fmaf_rn(al, lo(x), lo(y)), __fmaf_rn(al, hi(x), hi(y)));
+    }
+
+    static __device__ void run(const Args &a, const Ctx &cx)
+    {
+        const float al = a.alpha;
+        const int64_t gt = (int64_t)cx.block * cx.nthreads + cx.tid;
+        const int64_t stride = (int64_t)cx.grid * cx.nthreads;
+        int64_t done = 0;
+        if (aligned16(a.x) && aligned16(a.y) && aligned16(a.out)) {
+            const int64_t n8 = a.n >> 3;
+            int64_t i = gt;
+            for (; i + stride < n8; i += 2 * stride) {
+                const uint4 x0 = ldcs4u(a.x + 8 * i), y0 = ldcs4u(a.y + 8 * i);
+                const uint4 x1 = ldcs4u(a.x + 8 * (i + stride)), y1 = ldcs4u(a.y + 8 * (i + stride));
+                stcs4u(a.out + 8 * i, make_uint4(axpy2(al, x0.x, y0.x), axpy2(al, x0.y, y0.y),
+                                                 axpy2(al, x0.z, y0.z), axpy2(al, x0.w, y0.w)));
+                stcs4u(a.out + 8 * (i + stride),
+                       make_uint4(axpy2(al, x1.x, y1.x), axpy2(al, x1.y, y1.y),
+                                  axpy2(al, x1.z, y1.z), axpy2(al, x1.w, y1.w)));
+            }
+            if (i < n8) {
+                const uint4 x0 = ldcs4u(a.x + 8 * i), y0 = ldcs4u(a.y + 8 * i);
+                stcs4u(a.out + 8 * i, make_uint4(axpy2(al, x0.x, y0.x), axpy2(al, x0.y, y0.y),
+                                                 axpy2(al, x0.z, y0.z), axpy2(al, x0.w, y0.w)));
+            }
+            done = n8 << 3;
+        }
+        for (int64_t i = done + gt; i < a.n; i += stride) {
+            const float r = __fmaf_rn(al, __uint_as_float((unsigned)a.x[i] << 16),
+                                      __uint_as_float((unsigned)a.y[i] << 16));
+            __nv_bfloat16 h = __float2bfloat16_rn(r);
+            a.out[i] = *reinterpret_cast<unsigned short *>(&h);
+        }
+    }
+};
+
+// ------------------------------------------------------------------------
+// Parametric stream template.  Each loop tile, a thread loads one 16-byte
+// group, round-trips it through its own slot of the interval's shared
+// buffer, applies k multiply-adds (k/4 rounds over all four components,
+// then k%4 more on the leading components) and stores it.  The first
+// barrier follows the staging, the others split the FMA rounds evenly.  All
+// threads run the same number of tiles so every barrier is uniform.
+struct BodyStreamTmpl {
+    using Args = hf_stream_tmpl_args;
+    static constexpr int kId = HF_BODY_STREAM_TMPL;
+    static constexpr int kBarriers = 4;   // at most
+
+    static __host__ size_t workspace_bytes(const Args &) { return 0; }
+    static __host__ size_t smem_bytes(int, const Args &a) { return (size_t)a.smem_bytes; }
+    static __host__ hf_status validate(const Args &a)
+    {
+        if (a.n < 0 || (a.n & 3) || a.k < 0 || a.k > 4096) return HF_ERR_INVALID;
+        if (a.n_barriers < 0 || a.n_barriers > 4) return HF_ERR_INVALID;
+        if (a.smem_bytes < 0 || a.smem_bytes > 49152 || (a.smem_bytes & 15)) return HF_ERR_INVALID;
+        if (a.n > 0 && (!a.x || !a.y || !aligned16(a.x) || !aligned16(a.y))) return HF_ERR_INVALID;
+        return HF_OK;
+    }
+
+    static __device__ __forceinline__ void round4(float4 &v, float m, float b)
+    {
+        v.x = __fmaf_rn(v.x, m, b);
+        v.y = __fmaf_rn(v.y, m, b);
+        v.z = __fmaf_rn(v.z, m, b);
+        v.w = __fmaf_rn(v.w, m, b);
+    }
+
+    static __device__ void run(const Args &a, const Ctx &cx)
+    {
+        const int64_t n4 = a.n >> 2;
+        const int64_t stride = (int64_t)cx.grid * cx.nthreads;
+        const int64_t tiles = (n4 + stride - 1) / stride;
+        const int nslots = a.smem_bytes >> 4;
+        const bool staged = cx.tid < nslots;
+        const unsigned slot = (unsigned)__cvta_generic_to_shared(cx.smem) + 16u * cx.tid;
+        const int k4 = a.k >> 2, kr = a.k & 3, nb = a.n_barriers;
+        const float m = a.a, b = a.b;
+        for (int64_t t = 0; t < tiles; ++t) {
+            const int64_t i = (int64_t)cx.block * cx.nthreads + cx.tid + t * stride;
+            const bool ok = i < n4;
+            float4 v = ok ? ldcs4(a.x + 4 * i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (staged)
+                asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(slot), "f"(v.x),
+                             "f"(v.y), "f"(v.z), "f"(v.w)
+                             : "memory");
+            if (nb >= 1) interval_sync(cx);
+            if (staged)
+                asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                             : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                             : "r"(slot)
+                             : "memory");
+            int done = 0;
+            for (int s = 1; s < nb; ++s) {
+                const int upto = (int)((int64_t)k4 * s / nb);
+#pragma unroll 4
+                for (; done < upto; ++done) round4(v, m, b);
+                interval_sync(cx);
+            }
+#pragma unroll 4
+            for (; done < k4; ++done) round4(v, m, b);
+            if (kr > 0) v.x = __fmaf_rn(v.x, m, b);
+            if (kr > 1) v.y = __fmaf_rn(v.y, m, b);
+            if (kr > 2) v.z = __fmaf_rn(v.z, m, b);
+            if (ok) stcs4(a.y + 4 * i, v);
+        }
+    }
+};
+
+} // namespace hf

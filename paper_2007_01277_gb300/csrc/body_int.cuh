@@ -1,0 +1,149 @@
+// body_int.cuh -- the integer bodies: the 256-bin byte histogram (the
+// kernelHistogram1D kernel of Sec. 2.3, shared-memory atomics between two
+// block barriers) and the Philox4x32-10 counter-based generator (Salmon,
+// Moraes, Dror & Shaw, SC'11).
+#pragma once
+#include "hf_device.cuh"
+
+namespace hf {
+
+// ------------------------------------------------------------------------
+// Histogram.  Each warp of the interval owns a private 256-counter copy in
+// shared memory (1 KB), which keeps same-bin conflicts inside one warp.  The
+// three phases of Sec. 2.3 are kept: zero the copies, barrier, count every
+// byte with a shared atomic, barrier, merge the copies into the global bins
+// with one atomic per non-empty bin.  Bytes stream in as 128-bit loads, four
+// in flight per thread.
+struct BodyHist {
+    using Args = hf_hist256_args;
+    static constexpr int kId = HF_BODY_HIST256;
+    static constexpr int kBarriers = 2;
+
+    static __host__ size_t workspace_bytes(const Args &) { return 0; }
+    static __host__ size_t smem_bytes(int nthreads, const Args &)
+    {
+        return (size_t)(nthreads / 32) * 256 * sizeof(unsigned);
+    }
+    static __host__ hf_status validate(const Args &a)
+    {
+        if (a.n < 0) return HF_ERR_INVALID;
+        if (a.n > 0 && (!a.x || !a.bins)) return HF_ERR_INVALID;
+        return HF_OK;
+    }
+
+    static __device__ __forceinline__ void count_word(unsigned *h, unsigned w)
+    {
+        atomicAdd(h + (w & 0xffu), 1u);
+        atomicAdd(h + ((w >> 8) & 0xffu), 1u);
+        atomicAdd(h + ((w >> 16) & 0xffu), 1u);
+        atomicAdd(h + (w >> 24), 1u);
+    }
+    static __device__ __forceinline__ void count16(unsigned *h, uint4 v)
+    {
+        count_word(h, v.x);
+        count_word(h, v.y);
+        count_word(h, v.z);
+        count_word(h, v.w);
+    }
+
+    static __device__ void run(const Args &a, const Ctx &cx)
+    {
+        unsigned *sh = reinterpret_cast<unsigned *>(cx.smem);
+        const int nw = cx.nthreads >> 5;
+        for (int i = cx.tid; i < nw * 256; i += cx.nthreads) sh[i] = 0u;
+        interval_sync(cx);
+
+        unsigned *mine = sh + (cx.tid >> 5) * 256;
+        const int64_t gt = (int64_t)cx.block * cx.nthreads + cx.tid;
+        const int64_t stride = (int64_t)cx.grid * cx.nthreads;
+        int64_t done = 0;   // bytes handled by the vector loop
+        if (aligned16(a.x)) {
+            const int64_t n16 = a.n >> 4;
+            const uint8_t *x = a.x;
+            int64_t i = gt;
+            for (; i + 3 * stride < n16; i += 4 * stride) {
+                uint4 v0 = ldcs4u(x + 16 * i);
+                uint4 v1 = ldcs4u(x + 16 * (i + stride));
+                uint4 v2 = ldcs4u(x + 16 * (i + 2 * stride));
+                uint4 v3 = ldcs4u(x + 16 * (i + 3 * stride));
+                count16(mine, v0);
+                count16(mine, v1);
+                count16(mine, v2);
+                count16(mine, v3);
+            }
+            for (; i < n16; i += stride) count16(mine, ldcs4u(x + 16 * i));
+            done = n16 << 4;
+        }
+        for (int64_t i = done + gt; i < a.n; i += stride) atomicAdd(mine + a.x[i], 1u);
+        interval_sync(cx);
+
+        for (int b = cx.tid; b < 256; b += cx.nthreads) {
+            unsigned s = 0;
+            for (int w = 0; w < nw; ++w) s += sh[w * 256 + b];
+            if (s) atomicAdd(a.bins + b, s);
+        }
+    }
+};
+
+// ------------------------------------------------------------------------
+// Philox4x32-10.  Output i is the block for counter (lo32(first+i),
+// hi32(first+i), 0, 0) under key (lo32(seed), hi32(seed)); each of the ten
+// rounds multiplies two counter words by the Philox multipliers, mixes the
+// high halves with the other words and the round key, and the key advances
+// by the Weyl increments between rounds.  Two blocks per thread iteration
+// give the integer pipes two independent chains; blocks leave as 128-bit
+// streaming stores.
+struct BodyPhilox {
+    using Args = hf_philox_args;
+    static constexpr int kId = HF_BODY_PHILOX;
+    static constexpr int kBarriers = 0;
+    static constexpr unsigned kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
+    static constexpr unsigned kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;
+
+    static __host__ size_t workspace_bytes(const Args &) { return 0; }
+    static __host__ size_t smem_bytes(int, const Args &) { return 0; }
+    static __host__ hf_status validate(const Args &a)
+    {
+        if (a.n < 0) return HF_ERR_INVALID;
+        if (a.n > 0 && !a.out) return HF_ERR_INVALID;
+        if (a.n > 0 && !aligned16(a.out)) return HF_ERR_INVALID;
+        return HF_OK;
+    }
+
+    static __device__ __forceinline__ uint4 block(uint64_t ctr, unsigned k0, unsigned k1)
+    {
+        unsigned c0 = (unsigned)ctr, c1 = (unsigned)(ctr >> 32), c2 = 0u, c3 = 0u;
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+            const uint64_t p0 = (uint64_t)kM0 * c0;
+            const uint64_t p1 = (uint64_t)kM1 * c2;
+            const unsigned n0 = (unsigned)(p1 >> 32) ^ c1 ^ k0;
+            const unsigned n2 = (unsigned)(p0 >> 32) ^ c3 ^ k1;
+            c1 = (unsigned)p1;
+            c3 = (unsigned)p0;
+            c0 = n0;
+            c2 = n2;
+            k0 += kW0;
+            k1 += kW1;
+        }
+        return make_uint4(c0, c1, c2, c3);
+    }
+
+    static __device__ void run(const Args &a, const Ctx &cx)
+    {
+        const unsigned k0 = (unsigned)a.seed, k1 = (unsigned)(a.seed >> 32);
+        const int64_t gt = (int64_t)cx.block * cx.nthreads + cx.tid;
+        const int64_t stride = (int64_t)cx.grid * cx.nthreads;
+        uint4 *out = reinterpret_cast<uint4 *>(a.out);
+        int64_t i = gt;
+        for (; i + stride < a.n; i += 2 * stride) {
+            const uint4 u = block(a.first + (uint64_t)i, k0, k1);
+            const uint4 v = block(a.first + (uint64_t)(i + stride), k0, k1);
+            __stcs(out + i, u);
+            __stcs(out + i + stride, v);
+        }
+        if (i < a.n) __stcs(out + i, block(a.first + (uint64_t)i, k0, k1));
+    }
+};
+
+} // namespace hf

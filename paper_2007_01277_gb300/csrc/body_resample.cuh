@@ -1,0 +1,413 @@
+// body_resample.cuh -- the three image-rearranging bodies of Sec. 4.1:
+// bilinear x2 upsampling, 3x3/s2/p1 max pooling and 3x3/s1/p1 im2col.
+//
+// All three are HBM-bound.  The vector paths give each warp a strip of rows
+// of one plane: lane l holds input columns 4l..4l+3 of a 128-column band as
+// one 128-bit load, the one-column halo comes from the neighbouring lane by
+// shuffle, rows slide through registers so each input row is loaded once per
+// strip, the next rows are loaded before the current one is used, and
+// outputs leave as 128-bit (or 64-bit) streaming stores.  Shapes the vector
+// path does not cover use a thread-per-output scalar path with the same
+// arithmetic.
+#pragma once
+#include "hf_device.cuh"
+
+namespace hf {
+
+// ------------------------------------------------------------------------
+// Bilinear x2, half-pixel centres.  Along one axis of length L, output 2i
+// blends input i-1 and i with weights 1/4, 3/4 (output 0 is input 0) and
+// output 2i+1 blends i and i+1 with 3/4, 1/4 (output 2L-1 is input L-1).
+// Each blend is one fused multiply-add of an exactly scaled quarter, so it
+// is correctly rounded; rows are blended horizontally first, then
+// vertically, the order of the two-level formula.
+struct BodyUpsample {
+    using Args = hf_upsample2x_args;
+    static constexpr int kId = HF_BODY_UPSAMPLE2X;
+    static constexpr int kRows = 8;    // input rows per warp strip
+    static constexpr int kBarriers = 0;
+
+    static __host__ size_t workspace_bytes(const Args &) { return 0; }
+    static __host__ size_t smem_bytes(int, const Args &) { return 0; }
+    static __host__ hf_status validate(const Args &a)
+    {
+        if (a.P < 0 || a.H < 0 || a.W < 0) return HF_ERR_INVALID;
+        if ((int64_t)a.P * a.H * a.W == 0) return HF_OK;
+        if (!a.x || !a.y) return HF_ERR_INVALID;
+        if ((int64_t)a.P * a.H * a.W * 4 >= (int64_t)1 << 40) return HF_ERR_INVALID;
+        return HF_OK;
+    }
+
+    static __device__ __forceinline__ float blend(float near, float far)
+    {
+        return __fmaf_rn(0.75f, near, __fmul_rn(0.25f, far));
+    }
+
+    struct Raw {
+        float4 q;
+        float left, right;   // halo columns fetched only at band edges
+    };
+
+    static __device__ __forceinline__ Raw load_row(const float *row, int c0, int W, bool act)
+    {
+        Raw r;
+        r.q = act ? ldg4(row + c0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int lane = lane_id();
+        r.left = 0.f;
+        r.right = 0.f;
+        if (act && lane == 0 && c0 > 0) r.left = __ldg(row + c0 - 1);
+        if (act && lane == 31 && c0 + 4 < W) r.right = __ldg(row + c0 + 4);
+        return r;
+    }
+
+    // Horizontal pass of one row: out[0..7] = outputs 2c0 .. 2c0+7.
+    static __device__ __forceinline__ void hpass(const Raw &r, int c0, int W, float h[8])
+    {
+        const int lane = lane_id();
+        float L = __shfl_up_sync(0xffffffffu, r.q.w, 1);
+        float R = __shfl_down_sync(0xffffffffu, r.q.x, 1);
+        if (lane == 0) L = r.left;
+        if (lane == 31) R = r.right;
+        const float C[4] = {r.q.x, r.q.y, r.q.z, r.q.w};
+        const float Lf[4] = {L, r.q.x, r.q.y, r.q.z};
+        const float Rt[4] = {r.q.y, r.q.z, r.q.w, R};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int col = c0 + i;
+            h[2 * i] = col == 0 ? C[i] : blend(C[i], Lf[i]);
+            h[2 * i + 1] = col == W - 1 ? C[i] : blend(C[i], Rt[i]);
+        }
+    }
+
+    static __device__ void run_vec(const Args &a, const Ctx &cx)
+    {
+        const int H = a.H, W = a.W, Wo = 2 * W;
+        const int nb = (W + 127) / 128;
+        const int ns = (H + kRows - 1) / kRows;
+        const int64_t items = (int64_t)a.P * ns * nb;
+        const int nw = cx.nthreads >> 5;
+        const int lane = lane_id();
+        for (int64_t it = (int64_t)cx.block * nw + (cx.tid >> 5); it < items;
+             it += (int64_t)cx.grid * nw) {
+            const int b = (int)(it % nb);
+            const int64_t ps = it / nb;
+            const int s = (int)(ps % ns);
+            const int64_t p = ps / ns;
+            const int c0 = b * 128 + 4 * lane;
+            const bool act = c0 < W;
+            const float *xp = a.x + p * H * W;
+            float *yp = a.y + p * (int64_t)(2 * H) * Wo;
+            const int r0 = s * kRows;
+            const int r1 = min(r0 + kRows, H);
+            float hp[8], hc[8], hn[8];
+            Raw rn = load_row(xp + (int64_t)min(r0 + 1, H - 1) * W, c0, W, act);
+            if (r0 > 0) {
+                Raw rp = load_row(xp + (int64_t)(r0 - 1) * W, c0, W, act);
+                hpass(rp, c0, W, hp);
+            }
+            {
+                Raw rc = load_row(xp + (int64_t)r0 * W, c0, W, act);
+                hpass(rc, c0, W, hc);
+            }
+#pragma unroll 2
+            for (int r = r0; r < r1; ++r) {
+                // prefetch row r+2 while row r+1 is blended
+                Raw rf = load_row(xp + (int64_t)min(r + 2, H - 1) * W, c0, W, act);
+                hpass(rn, c0, W, hn);
+                float e[8], o[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    e[i] = r == 0 ? hc[i] : blend(hc[i], hp[i]);
+                    o[i] = r == H - 1 ? hc[i] : blend(hc[i], hn[i]);
+                }
+                if (act) {
+                    float *ye = yp + (int64_t)(2 * r) * Wo + 2 * c0;
+                    stcs4(ye, make_float4(e[0], e[1], e[2], e[3]));
+                    stcs4(ye + 4, make_float4(e[4], e[5], e[6], e[7]));
+                    float *yo = ye + Wo;
+                    stcs4(yo, make_float4(o[0], o[1], o[2], o[3]));
+                    stcs4(yo + 4, make_float4(o[4], o[5], o[6], o[7]));
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) hp[i] = hc[i], hc[i] = hn[i];
+                rn = rf;
+            }
+        }
+    }
+
+    static __device__ void run_scalar(const Args &a, const Ctx &cx)
+    {
+        const int H = a.H, W = a.W, Ho = 2 * H, Wo = 2 * W;
+        const int64_t total = (int64_t)a.P * Ho * Wo;
+        for (int64_t i = (int64_t)cx.block * cx.nthreads + cx.tid; i < total;
+             i += (int64_t)cx.grid * cx.nthreads) {
+            const int ox = (int)(i % Wo);
+            const int oy = (int)((i / Wo) % Ho);
+            const int64_t p = i / ((int64_t)Wo * Ho);
+            const float *xp = a.x + p * H * W;
+            auto hrow = [&](int y) {
+                const int c = ox >> 1;
+                const float C = __ldg(xp + (int64_t)y * W + c);
+                if (ox & 1)
+                    return c == W - 1 ? C : blend(C, __ldg(xp + (int64_t)y * W + c + 1));
+                return c == 0 ? C : blend(C, __ldg(xp + (int64_t)y * W + c - 1));
+            };
+            const int r = oy >> 1;
+            const float hc = hrow(r);
+            float v;
+            if (oy & 1)
+                v = r == H - 1 ? hc : blend(hc, hrow(r + 1));
+            else
+                v = r == 0 ? hc : blend(hc, hrow(r - 1));
+            a.y[i] = v;
+        }
+    }
+
+    static __device__ void run(const Args &a, const Ctx &cx)
+    {
+        if ((int64_t)a.P * a.H * a.W == 0) return;
+        if ((a.W & 3) == 0 && aligned16(a.x) && aligned16(a.y))
+            run_vec(a, cx);
+        else
+            run_scalar(a, cx);
+    }
+};
+
+// ------------------------------------------------------------------------
+// 3x3 max pooling, stride 2, padding 1 (padding never wins).
+struct BodyMaxpool {
+    using Args = hf_maxpool3s2_args;
+    static constexpr int kId = HF_BODY_MAXPOOL3S2;
+    static constexpr int kRows = 8;    // output rows per warp strip
+    static constexpr int kBarriers = 0;
+
+    static __host__ size_t workspace_bytes(const Args &) { return 0; }
+    static __host__ size_t smem_bytes(int, const Args &) { return 0; }
+    static __host__ hf_status validate(const Args &a)
+    {
+        if (a.P < 0 || a.H < 0 || a.W < 0) return HF_ERR_INVALID;
+        if ((int64_t)a.P * a.H * a.W == 0) return HF_OK;
+        if (!a.x || !a.y) return HF_ERR_INVALID;
+        if ((int64_t)a.P * a.H * a.W >= (int64_t)1 << 40) return HF_ERR_INVALID;
+        return HF_OK;
+    }
+
+    static __device__ __forceinline__ float mx(float u, float v) { return v > u ? v : u; }
+
+    struct Raw {
+        float4 q;
+        float left;
+    };
+    static __device__ __forceinline__ Raw load_row(const float *row, int c0, bool act, bool valid)
+    {
+        const float ninf = -__int_as_float(0x7f800000);
+        Raw r;
+        r.q = (act && valid) ? ldg4(row + c0) : make_float4(ninf, ninf, ninf, ninf);
+        r.left = ninf;
+        if (act && valid && lane_id() == 0 && c0 > 0) r.left = __ldg(row + c0 - 1);
+        return r;
+    }
+    // Horizontal 3-wide maxima centred on input columns c0 and c0+2.
+    static __device__ __forceinline__ float2 hmax(const Raw &r)
+    {
+        float L = __shfl_up_sync(0xffffffffu, r.q.w, 1);
+        if (lane_id() == 0) L = r.left;
+        return make_float2(mx(mx(L, r.q.x), r.q.y), mx(mx(r.q.y, r.q.z), r.q.w));
+    }
+
+    static __device__ void run_vec(const Args &a, const Ctx &cx)
+    {
+        const int H = a.H, W = a.W, Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1;
+        const int nb = (W + 127) / 128;
+        const int ns = (Ho + kRows - 1) / kRows;
+        const int64_t items = (int64_t)a.P * ns * nb;
+        const int nw = cx.nthreads >> 5;
+        const int lane = lane_id();
+        for (int64_t it = (int64_t)cx.block * nw + (cx.tid >> 5); it < items;
+             it += (int64_t)cx.grid * nw) {
+            const int b = (int)(it % nb);
+            const int64_t ps = it / nb;
+            const int s = (int)(ps % ns);
+            const int64_t p = ps / ns;
+            const int c0 = b * 128 + 4 * lane;
+            const bool act = c0 < W;
+            const float *xp = a.x + p * H * W;
+            float *yp = a.y + p * (int64_t)Ho * Wo;
+            const int o0 = s * kRows, o1 = min(o0 + kRows, Ho);
+            // carried: horizontal maxima of input row 2*oy - 1
+            float2 top = hmax(load_row(xp + (int64_t)(2 * o0 - 1) * W, c0, act, o0 > 0));
+            Raw ra = load_row(xp + (int64_t)(2 * o0) * W, c0, act, 2 * o0 < H);
+            Raw rb = load_row(xp + (int64_t)(2 * o0 + 1) * W, c0, act, 2 * o0 + 1 < H);
+#pragma unroll 2
+            for (int oy = o0; oy < o1; ++oy) {
+                const int n0 = 2 * oy + 2, n1 = 2 * oy + 3;
+                Raw na = load_row(xp + (int64_t)n0 * W, c0, act, oy + 1 < o1 && n0 < H);
+                Raw nbr = load_row(xp + (int64_t)n1 * W, c0, act, oy + 1 < o1 && n1 < H);
+                const float2 m0 = hmax(ra), m1 = hmax(rb);
+                const float2 v = make_float2(mx(mx(top.x, m0.x), m1.x), mx(mx(top.y, m0.y), m1.y));
+                if (act) stcs2(yp + (int64_t)oy * Wo + (c0 >> 1), v);
+                top = m1;
+                ra = na;
+                rb = nbr;
+            }
+        }
+    }
+
+    static __device__ void run_scalar(const Args &a, const Ctx &cx)
+    {
+        const int H = a.H, W = a.W, Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1;
+        const int64_t total = (int64_t)a.P * Ho * Wo;
+        const float ninf = -__int_as_float(0x7f800000);
+        for (int64_t i = (int64_t)cx.block * cx.nthreads + cx.tid; i < total;
+             i += (int64_t)cx.grid * cx.nthreads) {
+            const int ox = (int)(i % Wo);
+            const int oy = (int)((i / Wo) % Ho);
+            const int64_t p = i / ((int64_t)Wo * Ho);
+            const float *xp = a.x + p * H * W;
+            float m = ninf;
+            for (int ky = 0; ky < 3; ++ky) {
+                const int iy = 2 * oy - 1 + ky;
+                if (iy < 0 || iy >= H) continue;
+                for (int kx = 0; kx < 3; ++kx) {
+                    const int ix = 2 * ox - 1 + kx;
+                    if (ix < 0 || ix >= W) continue;
+                    m = mx(m, __ldg(xp + (int64_t)iy * W + ix));
+                }
+            }
+            a.y[i] = m;
+        }
+    }
+
+    static __device__ void run(const Args &a, const Ctx &cx)
+    {
+        if ((int64_t)a.P * a.H * a.W == 0) return;
+        if ((a.W & 3) == 0 && aligned16(a.x) && aligned16(a.y))
+            run_vec(a, cx);
+        else
+            run_scalar(a, cx);
+    }
+};
+
+// ------------------------------------------------------------------------
+// im2col, 3x3 window, stride 1, padding 1.  Vector path (W % 4 == 0,
+// W <= 64): a warp takes one (n, c) plane, each half-warp half of its
+// output rows; lane holds 4 columns of three consecutive input rows and
+// writes the nine shifted copies (ky, kx) of its columns for each row.
+struct BodyIm2col {
+    using Args = hf_im2col3_args;
+    static constexpr int kId = HF_BODY_IM2COL3;
+    static constexpr int kBarriers = 0;
+
+    static __host__ size_t workspace_bytes(const Args &) { return 0; }
+    static __host__ size_t smem_bytes(int, const Args &) { return 0; }
+    static __host__ hf_status validate(const Args &a)
+    {
+        if (a.N < 0 || a.C < 0 || a.H < 0 || a.W < 0) return HF_ERR_INVALID;
+        if ((int64_t)a.N * a.C * a.H * a.W == 0) return HF_OK;
+        if (!a.x || !a.col) return HF_ERR_INVALID;
+        if ((int64_t)a.N * a.C * a.H * a.W * 9 >= (int64_t)1 << 40) return HF_ERR_INVALID;
+        return HF_OK;
+    }
+
+    struct Row {
+        float4 q;
+        float L, R;   // columns c0-1 and c0+4 (0 outside the image)
+    };
+
+    static __device__ __forceinline__ float4 load(const float *xp, int iy, int H, int W, int c0,
+                                                  bool act)
+    {
+        const bool ok = act && iy >= 0 && iy < H;
+        return ok ? ldg4(xp + (int64_t)iy * W + c0) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    static __device__ __forceinline__ Row halo(float4 q, int c0, int W)
+    {
+        Row r;
+        r.q = q;
+        const int sub = lane_id() & 15;
+        r.L = __shfl_up_sync(0xffffffffu, q.w, 1);
+        r.R = __shfl_down_sync(0xffffffffu, q.x, 1);
+        if (sub == 0) r.L = 0.f;
+        if (c0 + 4 >= W) r.R = 0.f;
+        return r;
+    }
+
+    // The three kx-shifted copies of one input row (rows ky*3 + 0..2).
+    static __device__ __forceinline__ void emit(const Row &r, float *base, int64_t HW)
+    {
+        stcs4(base, make_float4(r.L, r.q.x, r.q.y, r.q.z));
+        stcs4(base + HW, r.q);
+        stcs4(base + 2 * HW, make_float4(r.q.y, r.q.z, r.q.w, r.R));
+    }
+
+    static __device__ void run_vec(const Args &a, const Ctx &cx)
+    {
+        const int H = a.H, W = a.W;
+        const int64_t HW = (int64_t)H * W;
+        const int64_t planes = (int64_t)a.N * a.C;
+        const int nw = cx.nthreads >> 5;
+        const int lane = lane_id();
+        const int half = lane >> 4;
+        const int c0 = 4 * (lane & 15);
+        const bool act = c0 < W;
+        const int hh = (H + 1) / 2;            // rows per half-warp
+        for (int64_t pl = (int64_t)cx.block * nw + (cx.tid >> 5); pl < planes;
+             pl += (int64_t)cx.grid * nw) {
+            const int64_t n = pl / a.C;
+            const int c = (int)(pl - n * a.C);
+            const float *xp = a.x + pl * HW;
+            float *cp = a.col + (n * a.C * 9 + (int64_t)c * 9) * HW;
+            const int oyb = half * hh;
+            const int oye = min(oyb + hh, H);
+            Row up = halo(load(xp, oyb - 1, H, W, c0, act), c0, W);
+            Row mid = halo(load(xp, oyb, H, W, c0, act), c0, W);
+            float4 nq = load(xp, oyb + 1, H, W, c0, act);
+#pragma unroll 2
+            for (int i = 0; i < hh; ++i) {
+                const int oy = oyb + i;
+                const bool valid = act && oy < oye;
+                float4 fq = load(xp, oy + 2, H, W, c0, act && oy + 1 < oye);
+                Row dn = halo(nq, c0, W);
+                if (valid) {
+                    float *base = cp + (int64_t)oy * W + c0;
+                    emit(up, base, HW);
+                    emit(mid, base + 3 * HW, HW);
+                    emit(dn, base + 6 * HW, HW);
+                }
+                up = mid;
+                mid = dn;
+                nq = fq;
+            }
+        }
+    }
+
+    static __device__ void run_scalar(const Args &a, const Ctx &cx)
+    {
+        const int H = a.H, W = a.W;
+        const int64_t HW = (int64_t)H * W;
+        const int64_t total = (int64_t)a.N * a.C * 9 * HW;
+        for (int64_t i = (int64_t)cx.block * cx.nthreads + cx.tid; i < total;
+             i += (int64_t)cx.grid * cx.nthreads) {
+            const int64_t pix = i % HW;
+            const int64_t row = i / HW;            // n*C*9 + c*9 + ky*3 + kx
+            const int k = (int)(row % 9);
+            const int64_t plane = row / 9;         // n*C + c
+            const int oy = (int)(pix / W), ox = (int)(pix % W);
+            const int iy = oy + k / 3 - 1, ix = ox + k % 3 - 1;
+            float v = 0.f;
+            if (iy >= 0 && iy < H && ix >= 0 && ix < W) v = __ldg(a.x + plane * HW + (int64_t)iy * W + ix);
+            a.col[i] = v;
+        }
+    }
+
+    static __device__ void run(const Args &a, const Ctx &cx)
+    {
+        if ((int64_t)a.N * a.C * a.H * a.W == 0) return;
+        if ((a.W & 3) == 0 && a.W <= 64 && aligned16(a.x) && aligned16(a.col))
+            run_vec(a, cx);
+        else
+            run_scalar(a, cx);
+    }
+};
+
+} // namespace hf

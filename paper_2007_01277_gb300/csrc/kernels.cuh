@@ -1,0 +1,250 @@
+// kernels.cuh -- the kernels that host the bodies: a standalone launch, the
+// 2-way horizontally fused kernel of Algorithm 1 (Sec. 3.1) and the N-way
+// persistent fused kernel, plus their type-erased host launchers.
+//
+// 2-way fused kernel (Algorithm 1):
+//   prologue   tid_k = threadIdx.x - offset_k, size_k = d_k  (the Ctx)
+//   barriers   body k uses "bar.sync id_k, d_k": id 1 for the low interval,
+//              id 2 for the high one (Sec. 3.1)
+//   guards     warps below the split run one body, the rest the other; the
+//              branch is warp-uniform (the split is a multiple of 32), the
+//              structured form of the goto/label guards of Algorithm 1
+//   resources  dynamic shared memory = low slice + high slice (128-byte
+//              aligned); registers are what the compiler needs for both
+//              bodies, optionally bounded by __maxnreg__ (Algorithm 2's r0)
+#pragma once
+#include <cstring>
+
+#include "body_bn.cuh"
+#include "body_fp.cuh"
+#include "body_int.cuh"
+#include "body_resample.cuh"
+
+namespace hf {
+
+// ------------------------------------------------------------------ single
+template <class B>
+struct SingleParams {
+    typename B::Args a;
+};
+
+template <class B>
+__device__ __forceinline__ void single_body(const SingleParams<B> &p)
+{
+    extern __shared__ __align__(128) unsigned char hf_smem[];
+    Ctx c;
+    c.tid = threadIdx.x;
+    c.nthreads = blockDim.x;
+    c.bar = 0;   // standalone: the block barrier, as the original kernel had
+    c.block = blockIdx.x;
+    c.grid = gridDim.x;
+    c.smem = hf_smem;
+    B::run(p.a, c);
+}
+
+template <class B>
+__global__ void k_single(const __grid_constant__ SingleParams<B> p)
+{
+    single_body<B>(p);
+}
+
+// ------------------------------------------------------------------ pair
+template <class A, class B>
+struct PairParams {
+    typename A::Args a;
+    typename B::Args b;
+    int w_split;        // warps in the low interval
+    int n_low, n_high;  // threads in the low / high interval
+    unsigned smem_high; // byte offset of the high interval's shared slice
+    int low_is_a;       // 1: body A runs on the low interval
+};
+
+template <class A, class B>
+__device__ __forceinline__ void pair_body(const PairParams<A, B> &p)
+{
+    extern __shared__ __align__(128) unsigned char hf_smem[];
+    const bool low = (int)(threadIdx.x >> 5) < p.w_split;
+    Ctx c;
+    c.block = blockIdx.x;
+    c.grid = gridDim.x;
+    if (low) {
+        c.tid = threadIdx.x;
+        c.nthreads = p.n_low;
+        c.bar = 1;
+        c.smem = hf_smem;
+    } else {
+        c.tid = threadIdx.x - p.n_low;
+        c.nthreads = p.n_high;
+        c.bar = 2;
+        c.smem = hf_smem + p.smem_high;
+    }
+    if (low == (p.low_is_a != 0))
+        A::run(p.a, c);
+    else
+        B::run(p.b, c);
+}
+
+template <class A, class B>
+__global__ void k_pair(const __grid_constant__ PairParams<A, B> p)
+{
+    pair_body<A, B>(p);
+}
+
+template <class A, class B, int R>
+__global__ void __maxnreg__(R) k_pair_cap(const __grid_constant__ PairParams<A, B> p)
+{
+    pair_body<A, B>(p);
+}
+
+// ------------------------------------------------------------------ N-way
+constexpr int kNwayBlob = 4096;
+
+struct NwayParams {
+    int n_int;                                  // intervals
+    int warp_begin[HF_MAX_INTERVALS + 1];       // interval i = warps [wb[i], wb[i+1])
+    unsigned smem_off[HF_MAX_INTERVALS];        // shared slice of interval i
+    int n_sched;                                // kernels
+    int sched_body[HF_MAX_SCHEDULE];            // body id of kernel j
+    int sched_int[HF_MAX_SCHEDULE];             // interval of kernel j
+    unsigned args_off[HF_MAX_SCHEDULE];         // argument block of kernel j in blob
+    alignas(16) unsigned char blob[kNwayBlob];
+};
+
+__device__ __forceinline__ void dispatch(int body, const unsigned char *args, const Ctx &c)
+{
+    switch (body) {
+    case HF_BODY_BN_STATS: BodyBn::run(*reinterpret_cast<const BodyBn::Args *>(args), c); break;
+    case HF_BODY_UPSAMPLE2X:
+        BodyUpsample::run(*reinterpret_cast<const BodyUpsample::Args *>(args), c);
+        break;
+    case HF_BODY_MAXPOOL3S2:
+        BodyMaxpool::run(*reinterpret_cast<const BodyMaxpool::Args *>(args), c);
+        break;
+    case HF_BODY_IM2COL3:
+        BodyIm2col::run(*reinterpret_cast<const BodyIm2col::Args *>(args), c);
+        break;
+    case HF_BODY_HIST256: BodyHist::run(*reinterpret_cast<const BodyHist::Args *>(args), c); break;
+    case HF_BODY_PHILOX:
+        BodyPhilox::run(*reinterpret_cast<const BodyPhilox::Args *>(args), c);
+        break;
+    case HF_BODY_POLY: BodyPoly::run(*reinterpret_cast<const BodyPoly::Args *>(args), c); break;
+    case HF_BODY_BF16_AXPY:
+        BodyBf16Axpy::run(*reinterpret_cast<const BodyBf16Axpy::Args *>(args), c);
+        break;
+    case HF_BODY_STREAM_TMPL:
+        BodyStreamTmpl::run(*reinterpret_cast<const BodyStreamTmpl::Args *>(args), c);
+        break;
+    default: break;
+    }
+}
+
+__device__ __forceinline__ void nway_body(const NwayParams &p)
+{
+    extern __shared__ __align__(128) unsigned char hf_smem[];
+    const int warp = threadIdx.x >> 5;
+    int i = 0;
+    while (i + 1 < p.n_int && warp >= p.warp_begin[i + 1]) ++i;
+    Ctx c;
+    c.tid = threadIdx.x - 32 * p.warp_begin[i];
+    c.nthreads = 32 * (p.warp_begin[i + 1] - p.warp_begin[i]);
+    c.bar = i + 1;
+    c.block = blockIdx.x;
+    c.grid = gridDim.x;
+    c.smem = hf_smem + p.smem_off[i];
+    bool first = true;
+    for (int j = 0; j < p.n_sched; ++j) {
+        if (p.sched_int[j] != i) continue;
+        // kernels sharing an interval share its shared slice: the previous
+        // one must be done with it before the next starts
+        if (!first) interval_sync(c);
+        first = false;
+        dispatch(p.sched_body[j], p.blob + p.args_off[j], c);
+    }
+}
+
+__global__ void k_nway(const __grid_constant__ NwayParams p);
+template <int R>
+__global__ void __maxnreg__(R) k_nway_cap(const __grid_constant__ NwayParams p)
+{
+    nway_body(p);
+}
+
+// ------------------------------------------------------------------ host side
+struct PairLaunch {
+    const void *const *args;   // [0] body A args, [1] body B args
+    int w_split, n_low, n_high;
+    unsigned smem_high, smem_total;
+    int low_is_a;
+    int grid, d0;
+};
+
+// Registry entry of one compiled instance.
+struct Instance {
+    int body_a, body_b;   // -1, -1 for the N-way kernel
+    int regcap;           // 0 = none
+    const void *func;     // the __global__ symbol
+    cudaError_t (*launch_pair)(const PairLaunch &, cudaStream_t);
+};
+
+template <class A, class B, int R>
+const void *pair_func()
+{
+    if constexpr (R == 0)
+        return reinterpret_cast<const void *>(&k_pair<A, B>);
+    else
+        return reinterpret_cast<const void *>(&k_pair_cap<A, B, R>);
+}
+
+template <class A, class B, int R>
+cudaError_t launch_pair(const PairLaunch &L, cudaStream_t s)
+{
+    PairParams<A, B> p;
+    std::memset(&p, 0, sizeof p);
+    std::memcpy(&p.a, L.args[0], sizeof(typename A::Args));
+    std::memcpy(&p.b, L.args[1], sizeof(typename B::Args));
+    p.w_split = L.w_split;
+    p.n_low = L.n_low;
+    p.n_high = L.n_high;
+    p.smem_high = L.smem_high;
+    p.low_is_a = L.low_is_a;
+    void *kargs[] = {&p};
+    return cudaLaunchKernel(pair_func<A, B, R>(), dim3(L.grid), dim3(L.d0), kargs, L.smem_total, s);
+}
+
+template <class A, class B, int R>
+Instance make_pair_instance()
+{
+    return Instance{A::kId, B::kId, R, pair_func<A, B, R>(), &launch_pair<A, B, R>};
+}
+
+// Table accessors implemented by the instantiation units.
+const Instance *pair_table_0(int *n);
+const Instance *pair_table_1(int *n);
+const Instance *pair_table_2(int *n);
+const Instance *pair_table_3(int *n);
+const Instance *nway_table(int *n);
+
+// Standalone kernels: one per body, no register bound.
+struct SingleEntry {
+    int body;
+    const void *func;
+    cudaError_t (*launch)(const void *args, int threads, int grid, unsigned smem, cudaStream_t);
+};
+
+template <class B>
+cudaError_t launch_single(const void *args, int threads, int grid, unsigned smem, cudaStream_t s)
+{
+    SingleParams<B> p;
+    std::memset(&p, 0, sizeof p);
+    std::memcpy(&p.a, args, sizeof(typename B::Args));
+    void *kargs[] = {&p};
+    return cudaLaunchKernel(reinterpret_cast<const void *>(&k_single<B>), dim3(grid),
+                            dim3(threads), kargs, smem, s);
+}
+
+const SingleEntry *single_table(int *n);
+
+// The register caps compiled for every fused pair and the N-way kernel.
+#define HF_REGCAP_LIST(X) X(32) X(40) X(48) X(64) X(96) X(128)
+
+} // namespace hf

@@ -1,0 +1,626 @@
+// runtime.cu -- the C ABI declared in include/hfuse.h: kernel registration,
+// 2-way and N-way fusion, validation, launch, resource queries and the
+// register bound of Algorithm 2 (Sec. 3.2).
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace hf;
+
+// ------------------------------------------------------------------ errors
+namespace {
+thread_local std::string g_last_error;
+
+hf_status fail(hf_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+#define HF_CUDA(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) return fail(HF_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// ------------------------------------------------------------------ body table
+struct BodyOps {
+    size_t args_size;
+    hf_status (*validate)(const void *);
+    size_t (*smem)(int, const void *);
+    size_t (*workspace)(const void *);
+    int barriers;
+    const char *name;
+};
+
+template <class B>
+BodyOps ops(const char *name)
+{
+    using A = typename B::Args;
+    return BodyOps{sizeof(A),
+                   [](const void *p) { return B::validate(*static_cast<const A *>(p)); },
+                   [](int n, const void *p) { return B::smem_bytes(n, *static_cast<const A *>(p)); },
+                   [](const void *p) { return B::workspace_bytes(*static_cast<const A *>(p)); },
+                   B::kBarriers, name};
+}
+
+const BodyOps &body_ops(int id)
+{
+    static const BodyOps kOps[HF_BODY_COUNT] = {
+        ops<BodyBn>("bn_stats"),     ops<BodyUpsample>("upsample2x"),
+        ops<BodyMaxpool>("maxpool3s2"), ops<BodyIm2col>("im2col3"),
+        ops<BodyHist>("hist256"),    ops<BodyPhilox>("philox"),
+        ops<BodyPoly>("poly"),       ops<BodyBf16Axpy>("bf16_axpy"),
+        ops<BodyStreamTmpl>("stream_tmpl")};
+    return kOps[id];
+}
+
+bool valid_body(int id) { return id >= 0 && id < HF_BODY_COUNT; }
+
+size_t align128(size_t v) { return (v + 127) / 128 * 128; }
+
+// ------------------------------------------------------------------ registry
+struct Registry {
+    std::vector<Instance> pairs, nway;
+    std::vector<SingleEntry> singles;
+    std::vector<int> caps;
+};
+
+const Registry &registry()
+{
+    static Registry r;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const Instance *(*tabs[])(int *) = {pair_table_0, pair_table_1, pair_table_2, pair_table_3};
+        for (auto t : tabs) {
+            int n = 0;
+            const Instance *p = t(&n);
+            r.pairs.insert(r.pairs.end(), p, p + n);
+        }
+        int n = 0;
+        const Instance *p = nway_table(&n);
+        r.nway.assign(p, p + n);
+        const SingleEntry *s = single_table(&n);
+        r.singles.assign(s, s + n);
+        for (auto &i : r.nway)
+            if (i.regcap) r.caps.push_back(i.regcap);
+        std::sort(r.caps.begin(), r.caps.end());
+    });
+    return r;
+}
+
+bool cap_ok(int regcap)
+{
+    if (regcap == 0) return true;
+    for (int c : registry().caps)
+        if (c == regcap) return true;
+    return false;
+}
+
+const Instance *find_nway(int regcap)
+{
+    for (auto &i : registry().nway)
+        if (i.regcap == regcap) return &i;
+    return nullptr;
+}
+
+const SingleEntry *find_single(int body)
+{
+    for (auto &s : registry().singles)
+        if (s.body == body) return &s;
+    return nullptr;
+}
+
+// ------------------------------------------------------------------ per-function state
+struct FuncInfo {
+    int regs = 0, local = 0, max_threads = 0;
+    size_t smem_set = 48 * 1024;
+};
+std::mutex g_mu;
+std::unordered_map<const void *, FuncInfo> g_funcs;   // keyed by symbol (one device)
+
+hf_status func_info(const void *f, FuncInfo *out)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_funcs.find(f);
+        if (it != g_funcs.end()) {
+            *out = it->second;
+            return HF_OK;
+        }
+    }
+    cudaFuncAttributes a;
+    HF_CUDA(cudaFuncGetAttributes(&a, f));
+    FuncInfo fi;
+    fi.regs = a.numRegs;
+    fi.local = (int)a.localSizeBytes;
+    fi.max_threads = a.maxThreadsPerBlock;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_funcs.emplace(f, fi);
+    *out = fi;
+    return HF_OK;
+}
+
+hf_status ensure_smem(const void *f, size_t smem)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    FuncInfo &fi = g_funcs[f];
+    if (smem <= fi.smem_set) return HF_OK;
+    HF_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    fi.smem_set = smem;
+    return HF_OK;
+}
+
+hf_status limits(hf_device_limits *lim)
+{
+    int dev = 0;
+    HF_CUDA(cudaGetDevice(&dev));
+    static std::mutex mu;
+    static std::unordered_map<int, hf_device_limits> cache;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(dev);
+        if (it != cache.end()) {
+            *lim = it->second;
+            return HF_OK;
+        }
+    }
+    cudaDeviceProp p;
+    HF_CUDA(cudaGetDeviceProperties(&p, dev));
+    hf_device_limits l;
+    l.sm_count = p.multiProcessorCount;
+    l.regs_per_sm = p.regsPerMultiprocessor;
+    l.smem_per_sm = (int)p.sharedMemPerMultiprocessor;
+    l.threads_per_sm = p.maxThreadsPerMultiProcessor;
+    l.smem_per_block_optin = (int)p.sharedMemPerBlockOptin;
+    l.l2_bytes = p.l2CacheSize;
+    l.cc_major = p.major;
+    l.cc_minor = p.minor;
+    std::lock_guard<std::mutex> lk(mu);
+    cache[dev] = l;
+    *lim = l;
+    return HF_OK;
+}
+
+hf_status check_threads(const hf_kernel_t *k, int t);
+
+} // namespace
+
+// ------------------------------------------------------------------ handles
+struct hf_kernel_t {
+    int body;
+    int tmin, tmax, gran;
+    std::string name;
+};
+
+struct hf_fused_t {
+    bool nway;
+    int regcap;
+    int d0;
+    // pair
+    int body_low, body_high, n_low, n_high;
+    const Instance *inst;
+    int low_is_a;   // instance body A runs on the low interval
+    // N-way
+    int n;
+    int sched_body[HF_MAX_SCHEDULE];
+    int sched_int[HF_MAX_SCHEDULE];
+    int n_int;
+    int int_threads[HF_MAX_INTERVALS];
+};
+
+namespace {
+hf_status check_threads(const hf_kernel_t *k, int t)
+{
+    if (t % 32 || t < k->tmin || t > k->tmax || t % k->gran)
+        return fail(HF_ERR_SPLIT, "%d threads outside kernel '%s' range [%d, %d] step %d", t,
+                    k->name.c_str(), k->tmin, k->tmax, k->gran);
+    return HF_OK;
+}
+
+struct Geometry {
+    const void *func;
+    unsigned smem_total;
+    int grid;
+};
+
+// Resident blocks of `func` at d0 threads and `smem` bytes -> grid.
+hf_status pick_grid(const void *func, int d0, size_t smem, int want, int *grid, int *bps)
+{
+    hf_device_limits lim;
+    hf_status s = limits(&lim);
+    if (s) return s;
+    if (smem > (size_t)lim.smem_per_block_optin)
+        return fail(HF_ERR_SMEM, "combined shared memory %zu B above the %d B per-block limit",
+                    smem, lim.smem_per_block_optin);
+    s = ensure_smem(func, smem);
+    if (s) return s;
+    int b = 0;
+    HF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, func, d0, smem));
+    if (b <= 0) return fail(HF_ERR_REGS, "block of %d threads with %zu B shared memory cannot be resident", d0, smem);
+    if (bps) *bps = b;
+    if (grid) *grid = want > 0 ? want : b * lim.sm_count;
+    return HF_OK;
+}
+
+hf_status pair_smem(const hf_fused_t *f, const void *const *uargs, unsigned *smem_high,
+                    unsigned *total)
+{
+    const size_t lo = align128(body_ops(f->body_low).smem(f->n_low, uargs[0]));
+    const size_t hi = align128(body_ops(f->body_high).smem(f->n_high, uargs[1]));
+    *smem_high = (unsigned)lo;
+    *total = (unsigned)(lo + hi);
+    return HF_OK;
+}
+
+hf_status validate_args(int body, const void *a, int which)
+{
+    if (!a) return fail(HF_ERR_INVALID, "argument block %d is NULL", which);
+    hf_status s = body_ops(body).validate(a);
+    if (s) return fail(s, "argument block %d (%s) rejected", which, body_ops(body).name);
+    return HF_OK;
+}
+
+// Builds the N-way parameter block; also used for pairs without a compiled
+// pair instance.
+hf_status nway_params(const hf_fused_t *f, const void *const *args, NwayParams *p, unsigned *smem)
+{
+    std::memset(p, 0, sizeof *p);
+    p->n_int = f->n_int;
+    int w = 0;
+    size_t off = 0;
+    for (int i = 0; i < f->n_int; ++i) {
+        p->warp_begin[i] = w;
+        w += f->int_threads[i] / 32;
+        size_t need = 0;
+        for (int j = 0; j < f->n; ++j)
+            if (f->sched_int[j] == i)
+                need = std::max(need, body_ops(f->sched_body[j]).smem(f->int_threads[i], args[j]));
+        p->smem_off[i] = (unsigned)off;
+        off += align128(need);
+    }
+    p->warp_begin[f->n_int] = w;
+    p->n_sched = f->n;
+    size_t boff = 0;
+    for (int j = 0; j < f->n; ++j) {
+        const size_t sz = body_ops(f->sched_body[j]).args_size;
+        boff = (boff + 15) / 16 * 16;
+        if (boff + sz > (size_t)kNwayBlob) return fail(HF_ERR_INVALID, "argument blocks exceed %d B", kNwayBlob);
+        std::memcpy(p->blob + boff, args[j], sz);
+        p->sched_body[j] = f->sched_body[j];
+        p->sched_int[j] = f->sched_int[j];
+        p->args_off[j] = (unsigned)boff;
+        boff += sz;
+    }
+    *smem = (unsigned)off;
+    return HF_OK;
+}
+} // namespace
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char *hf_status_string(hf_status s)
+{
+    switch (s) {
+    case HF_OK: return "ok";
+    case HF_ERR_INVALID: return "invalid argument";
+    case HF_ERR_SPLIT: return "invalid thread split";
+    case HF_ERR_BARRIER: return "too many barrier intervals";
+    case HF_ERR_SMEM: return "shared memory limit exceeded";
+    case HF_ERR_REGS: return "block too large for the register use";
+    case HF_ERR_UNSUPPORTED: return "configuration not compiled";
+    case HF_ERR_CUDA: return "CUDA runtime error";
+    case HF_ERR_TIMEOUT: return "timeout";
+    }
+    return "unknown status";
+}
+
+const char *hf_last_error(void) { return g_last_error.c_str(); }
+
+size_t hf_args_size(int body_id) { return valid_body(body_id) ? body_ops(body_id).args_size : 0; }
+
+int hf_regcaps(int *caps, int cap)
+{
+    const auto &c = registry().caps;
+    for (int i = 0; i < (int)c.size() && i < cap; ++i) caps[i] = c[i];
+    return (int)c.size();
+}
+
+hf_status hf_register_kernel(const hf_kernel_desc *d, hf_kernel *out)
+{
+    if (!d || !out) return fail(HF_ERR_INVALID, "NULL descriptor or output");
+    if (!valid_body(d->body_id)) return fail(HF_ERR_INVALID, "unknown body id %d", d->body_id);
+    const int tmin = d->min_threads ? d->min_threads : 32;
+    const int tmax = d->max_threads ? d->max_threads : 1024;
+    const int gran = d->thread_granularity ? d->thread_granularity : 32;
+    if (tmin % 32 || tmax % 32 || gran % 32 || tmin < 32 || tmax > 1024 || tmin > tmax || gran <= 0)
+        return fail(HF_ERR_INVALID, "thread range [%d, %d] step %d not warp aligned", tmin, tmax, gran);
+    hf_kernel_t *k = new hf_kernel_t{d->body_id, tmin, tmax, gran,
+                                     d->name ? d->name : body_ops(d->body_id).name};
+    *out = k;
+    return HF_OK;
+}
+
+void hf_destroy_kernel(hf_kernel k) { delete k; }
+
+hf_status hf_fuse(hf_kernel a, hf_kernel b, int split, int d0, int regcap, hf_fused *out)
+{
+    if (!a || !b || !out) return fail(HF_ERR_INVALID, "NULL kernel or output");
+    if (d0 % 32 || split % 32 || split <= 0 || split >= d0 || d0 > 1024)
+        return fail(HF_ERR_SPLIT, "split %d of block %d: need multiples of 32, 0 < split < d0 <= 1024", split, d0);
+    hf_status s = check_threads(a, split);
+    if (s) return s;
+    s = check_threads(b, d0 - split);
+    if (s) return s;
+    if (!cap_ok(regcap)) return fail(HF_ERR_UNSUPPORTED, "register cap %d not compiled", regcap);
+    hf_fused_t *f = new hf_fused_t();
+    f->regcap = regcap;
+    f->d0 = d0;
+    f->body_low = a->body;
+    f->body_high = b->body;
+    f->n_low = split;
+    f->n_high = d0 - split;
+    f->inst = nullptr;
+    for (auto &i : registry().pairs) {
+        if (i.regcap != regcap) continue;
+        if (i.body_a == a->body && i.body_b == b->body) {
+            f->inst = &i;
+            f->low_is_a = 1;
+            break;
+        }
+        if (i.body_a == b->body && i.body_b == a->body) {
+            f->inst = &i;
+            f->low_is_a = 0;
+            break;
+        }
+    }
+    if (!f->inst) {   // no compiled pair: the generic N-way kernel with two intervals
+        f->nway = true;
+        f->inst = find_nway(regcap);
+        f->n = 2;
+        f->n_int = 2;
+        f->sched_body[0] = a->body;
+        f->sched_body[1] = b->body;
+        f->sched_int[0] = 0;
+        f->sched_int[1] = 1;
+        f->int_threads[0] = split;
+        f->int_threads[1] = d0 - split;
+    }
+    FuncInfo fi;
+    s = func_info(f->inst->func, &fi);
+    if (s) {
+        delete f;
+        return s;
+    }
+    if (fi.max_threads < d0) {
+        delete f;
+        return fail(HF_ERR_REGS, "fused instance uses %d registers: at most %d threads per block, asked %d",
+                    fi.regs, fi.max_threads, d0);
+    }
+    *out = f;
+    return HF_OK;
+}
+
+hf_status hf_fuse_n(const hf_kernel *ks, int n, const int *interval_of, const int *interval_threads,
+                    int n_intervals, int regcap, hf_fused *out)
+{
+    if (!ks || !interval_of || !interval_threads || !out) return fail(HF_ERR_INVALID, "NULL argument");
+    if (n < 1 || n > HF_MAX_SCHEDULE) return fail(HF_ERR_INVALID, "%d kernels (1..%d)", n, HF_MAX_SCHEDULE);
+    if (n_intervals < 1) return fail(HF_ERR_INVALID, "no intervals");
+    if (n_intervals > HF_MAX_INTERVALS)
+        return fail(HF_ERR_BARRIER, "%d intervals: only %d named barrier ids", n_intervals, HF_MAX_INTERVALS);
+    int d0 = 0;
+    for (int i = 0; i < n_intervals; ++i) {
+        if (interval_threads[i] <= 0 || interval_threads[i] % 32)
+            return fail(HF_ERR_SPLIT, "interval %d has %d threads", i, interval_threads[i]);
+        d0 += interval_threads[i];
+    }
+    if (d0 > 1024) return fail(HF_ERR_SPLIT, "block of %d threads", d0);
+    std::vector<int> used(n_intervals, 0);
+    for (int j = 0; j < n; ++j) {
+        if (!ks[j]) return fail(HF_ERR_INVALID, "kernel %d is NULL", j);
+        if (interval_of[j] < 0 || interval_of[j] >= n_intervals)
+            return fail(HF_ERR_INVALID, "kernel %d on interval %d", j, interval_of[j]);
+        hf_status s = check_threads(ks[j], interval_threads[interval_of[j]]);
+        if (s) return s;
+        used[interval_of[j]] = 1;
+    }
+    for (int i = 0; i < n_intervals; ++i)
+        if (!used[i]) return fail(HF_ERR_INVALID, "interval %d runs no kernel", i);
+    if (!cap_ok(regcap)) return fail(HF_ERR_UNSUPPORTED, "register cap %d not compiled", regcap);
+    hf_fused_t *f = new hf_fused_t();
+    f->nway = true;
+    f->regcap = regcap;
+    f->d0 = d0;
+    f->inst = find_nway(regcap);
+    f->n = n;
+    f->n_int = n_intervals;
+    for (int j = 0; j < n; ++j) {
+        f->sched_body[j] = ks[j]->body;
+        f->sched_int[j] = interval_of[j];
+    }
+    for (int i = 0; i < n_intervals; ++i) f->int_threads[i] = interval_threads[i];
+    FuncInfo fi;
+    hf_status s = func_info(f->inst->func, &fi);
+    if (s) {
+        delete f;
+        return s;
+    }
+    if (fi.max_threads < d0) {
+        delete f;
+        return fail(HF_ERR_REGS, "N-way instance uses %d registers: at most %d threads per block", fi.regs,
+                    fi.max_threads);
+    }
+    *out = f;
+    return HF_OK;
+}
+
+void hf_destroy_fused(hf_fused f) { delete f; }
+
+hf_status hf_launch(hf_fused f, const void *const *args, int grid, void *stream)
+{
+    if (!f || !args) return fail(HF_ERR_INVALID, "NULL fused kernel or argument list");
+    if (grid < 0) return fail(HF_ERR_INVALID, "grid %d", grid);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!f->nway) {
+        hf_status s = validate_args(f->body_low, args[0], 0);
+        if (s) return s;
+        s = validate_args(f->body_high, args[1], 1);
+        if (s) return s;
+        unsigned smem_high, total;
+        pair_smem(f, args, &smem_high, &total);
+        int g = 0;
+        s = pick_grid(f->inst->func, f->d0, total, grid, &g, nullptr);
+        if (s) return s;
+        const void *iargs[2] = {f->low_is_a ? args[0] : args[1], f->low_is_a ? args[1] : args[0]};
+        PairLaunch L{iargs, f->n_low / 32, f->n_low, f->n_high, smem_high, total, f->low_is_a, g, f->d0};
+        HF_CUDA(f->inst->launch_pair(L, st));
+        return HF_OK;
+    }
+    for (int j = 0; j < f->n; ++j) {
+        hf_status s = validate_args(f->sched_body[j], args[j], j);
+        if (s) return s;
+    }
+    static thread_local NwayParams p;
+    unsigned smem = 0;
+    hf_status s = nway_params(f, args, &p, &smem);
+    if (s) return s;
+    int g = 0;
+    s = pick_grid(f->inst->func, f->d0, smem, grid, &g, nullptr);
+    if (s) return s;
+    void *kargs[] = {&p};
+    HF_CUDA(cudaLaunchKernel(f->inst->func, dim3(g), dim3(f->d0), kargs, smem, st));
+    return HF_OK;
+}
+
+hf_status hf_launch_single(hf_kernel k, const void *args, int threads, int grid, void *stream)
+{
+    if (!k) return fail(HF_ERR_INVALID, "NULL kernel");
+    if (grid < 0) return fail(HF_ERR_INVALID, "grid %d", grid);
+    hf_status s = check_threads(k, threads);
+    if (s) return s;
+    s = validate_args(k->body, args, 0);
+    if (s) return s;
+    const SingleEntry *e = find_single(k->body);
+    const size_t smem = align128(body_ops(k->body).smem(threads, args));
+    FuncInfo fi;
+    s = func_info(e->func, &fi);
+    if (s) return s;
+    if (fi.max_threads < threads)
+        return fail(HF_ERR_REGS, "kernel uses %d registers: at most %d threads", fi.regs, fi.max_threads);
+    int g = 0;
+    s = pick_grid(e->func, threads, smem, grid, &g, nullptr);
+    if (s) return s;
+    HF_CUDA(e->launch(args, threads, g, (unsigned)smem, static_cast<cudaStream_t>(stream)));
+    return HF_OK;
+}
+
+hf_status hf_query(hf_fused f, const void *const *args, hf_fused_info *info)
+{
+    if (!f || !args || !info) return fail(HF_ERR_INVALID, "NULL argument");
+    unsigned smem = 0;
+    if (!f->nway) {
+        unsigned hi;
+        pair_smem(f, args, &hi, &smem);
+    } else {
+        static thread_local NwayParams p;
+        hf_status s = nway_params(f, args, &p, &smem);
+        if (s) return s;
+    }
+    FuncInfo fi;
+    hf_status s = func_info(f->inst->func, &fi);
+    if (s) return s;
+    int bps = 0;
+    s = pick_grid(f->inst->func, f->d0, smem, 0, nullptr, &bps);
+    if (s) return s;
+    info->regs = fi.regs;
+    info->spill_bytes = fi.local;
+    info->smem_bytes = (int)smem;
+    info->block_threads = f->d0;
+    info->blocks_per_sm = bps;
+    info->max_threads_per_block = fi.max_threads;
+    info->n_intervals = f->nway ? f->n_int : 2;
+    return HF_OK;
+}
+
+hf_status hf_query_single(hf_kernel k, const void *args, int threads, hf_fused_info *info)
+{
+    if (!k || !args || !info) return fail(HF_ERR_INVALID, "NULL argument");
+    hf_status s = check_threads(k, threads);
+    if (s) return s;
+    const SingleEntry *e = find_single(k->body);
+    const size_t smem = align128(body_ops(k->body).smem(threads, args));
+    FuncInfo fi;
+    s = func_info(e->func, &fi);
+    if (s) return s;
+    int bps = 0;
+    s = pick_grid(e->func, threads, smem, 0, nullptr, &bps);
+    if (s) return s;
+    info->regs = fi.regs;
+    info->spill_bytes = fi.local;
+    info->smem_bytes = (int)smem;
+    info->block_threads = threads;
+    info->blocks_per_sm = bps;
+    info->max_threads_per_block = fi.max_threads;
+    info->n_intervals = 1;
+    return HF_OK;
+}
+
+hf_status hf_workspace_size(int body_id, const void *args, size_t *bytes)
+{
+    if (!valid_body(body_id) || !args || !bytes) return fail(HF_ERR_INVALID, "bad body id or NULL");
+    *bytes = body_ops(body_id).workspace(args);
+    return HF_OK;
+}
+
+hf_status hf_device_info(hf_device_limits *lim)
+{
+    if (!lim) return fail(HF_ERR_INVALID, "NULL output");
+    return limits(lim);
+}
+
+hf_status hf_register_bound(const hf_device_limits *lim, int d1, int nregs1, int d2, int nregs2,
+                            int smem_fused, int *r0)
+{
+    if (!lim || !r0 || d1 <= 0 || d2 <= 0 || nregs1 <= 0 || nregs2 <= 0 || smem_fused < 0)
+        return fail(HF_ERR_INVALID, "bad register-bound input");
+    const int d0 = d1 + d2;
+    // resident blocks the two original kernels reach on their registers
+    int b0 = std::min(lim->regs_per_sm / (d1 * nregs1), lim->regs_per_sm / (d2 * nregs2));
+    if (smem_fused > 0) b0 = std::min(b0, lim->smem_per_sm / smem_fused);
+    b0 = std::min(b0, lim->threads_per_sm / d0);
+    *r0 = b0 > 0 ? lim->regs_per_sm / (b0 * d0) : 0;
+    return HF_OK;
+}
+
+hf_status hf_stream_wait(void *stream, int timeout_ms)
+{
+    if (timeout_ms < 0) return fail(HF_ERR_INVALID, "negative timeout");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(st);
+        if (e == cudaSuccess) return HF_OK;
+        if (e != cudaErrorNotReady) return fail(HF_ERR_CUDA, "cudaStreamQuery: %s", cudaGetErrorString(e));
+        const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
+                            std::chrono::steady_clock::now() - t0).count();
+        if (ms >= timeout_ms) return fail(HF_ERR_TIMEOUT, "stream not done after %d ms", timeout_ms);
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+} // extern "C"

@@ -1,0 +1,295 @@
+"""Thin ctypes binding of libhfuse.so (the C ABI of include/hfuse.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  The entry points keep the C names (``hf_register_kernel``,
+``hf_fuse``, ``hf_launch`` ...); the helpers at the end build argument
+blocks from torch tensors, which serve only as device memory.  Importing this
+module loads the library and raises if it has not been built -- there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhfuse.so")
+
+HF_OK = 0
+STATUS = {0: "HF_OK", -1: "HF_ERR_INVALID", -2: "HF_ERR_SPLIT", -3: "HF_ERR_BARRIER",
+          -4: "HF_ERR_SMEM", -5: "HF_ERR_REGS", -6: "HF_ERR_UNSUPPORTED", -7: "HF_ERR_CUDA",
+          -8: "HF_ERR_TIMEOUT"}
+
+BN_STATS, UPSAMPLE2X, MAXPOOL3S2, IM2COL3, HIST256, PHILOX, POLY, BF16_AXPY, STREAM_TMPL = range(9)
+BODY_NAMES = ["bn_stats", "upsample2x", "maxpool3s2", "im2col3", "hist256", "philox", "poly",
+              "bf16_axpy", "stream_tmpl"]
+MAX_INTERVALS = 15
+MAX_SCHEDULE = 16
+
+_P = ctypes.c_void_p
+_i32, _i64, _u64, _f32 = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_float
+
+
+class BnStatsArgs(ctypes.Structure):
+    _fields_ = [("x", _P), ("mean", _P), ("var", _P), ("N", _i32), ("C", _i32), ("HW", _i32),
+                ("workspace", _P)]
+
+
+class Upsample2xArgs(ctypes.Structure):
+    _fields_ = [("x", _P), ("y", _P), ("P", _i32), ("H", _i32), ("W", _i32)]
+
+
+class Maxpool3s2Args(ctypes.Structure):
+    _fields_ = [("x", _P), ("y", _P), ("P", _i32), ("H", _i32), ("W", _i32)]
+
+
+class Im2col3Args(ctypes.Structure):
+    _fields_ = [("x", _P), ("col", _P), ("N", _i32), ("C", _i32), ("H", _i32), ("W", _i32)]
+
+
+class Hist256Args(ctypes.Structure):
+    _fields_ = [("x", _P), ("bins", _P), ("n", _i64)]
+
+
+class PhiloxArgs(ctypes.Structure):
+    _fields_ = [("out", _P), ("n", _i64), ("seed", _u64), ("first", _u64)]
+
+
+class PolyArgs(ctypes.Structure):
+    _fields_ = [("x", _P), ("y", _P), ("n", _i64), ("iters", _i32), ("coef", _f32 * 33)]
+
+
+class Bf16AxpyArgs(ctypes.Structure):
+    _fields_ = [("x", _P), ("y", _P), ("out", _P), ("n", _i64), ("alpha", _f32)]
+
+
+class StreamTmplArgs(ctypes.Structure):
+    _fields_ = [("x", _P), ("y", _P), ("n", _i64), ("k", _i32), ("n_barriers", _i32),
+                ("smem_bytes", _i32), ("a", _f32), ("b", _f32)]
+
+
+ARGS_TYPES = [BnStatsArgs, Upsample2xArgs, Maxpool3s2Args, Im2col3Args, Hist256Args, PhiloxArgs,
+              PolyArgs, Bf16AxpyArgs, StreamTmplArgs]
+
+
+class KernelDesc(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("body_id", _i32), ("min_threads", _i32),
+                ("max_threads", _i32), ("thread_granularity", _i32)]
+
+
+class FusedInfo(ctypes.Structure):
+    _fields_ = [("regs", _i32), ("spill_bytes", _i32), ("smem_bytes", _i32),
+                ("block_threads", _i32), ("blocks_per_sm", _i32),
+                ("max_threads_per_block", _i32), ("n_intervals", _i32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class DeviceLimits(ctypes.Structure):
+    _fields_ = [("sm_count", _i32), ("regs_per_sm", _i32), ("smem_per_sm", _i32),
+                ("threads_per_sm", _i32), ("smem_per_block_optin", _i32), ("l2_bytes", _i32),
+                ("cc_major", _i32), ("cc_minor", _i32)]
+
+
+class HFError(RuntimeError):
+    def __init__(self, fn, status, msg):
+        super().__init__("%s -> %s: %s" % (fn, STATUS.get(status, status), msg))
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            "libhfuse.so is not built (expected at %s); run __graft_entry__.build() or "
+            "python paper_2007_01277_gb300/build.py" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "hf_register_kernel": (_i32, [ctypes.POINTER(KernelDesc), ctypes.POINTER(_P)]),
+        "hf_destroy_kernel": (None, [_P]),
+        "hf_fuse": (_i32, [_P, _P, _i32, _i32, _i32, ctypes.POINTER(_P)]),
+        "hf_fuse_n": (_i32, [ctypes.POINTER(_P), _i32, ctypes.POINTER(_i32),
+                             ctypes.POINTER(_i32), _i32, _i32, ctypes.POINTER(_P)]),
+        "hf_destroy_fused": (None, [_P]),
+        "hf_launch": (_i32, [_P, ctypes.POINTER(_P), _i32, _P]),
+        "hf_launch_single": (_i32, [_P, _P, _i32, _i32, _P]),
+        "hf_query": (_i32, [_P, ctypes.POINTER(_P), ctypes.POINTER(FusedInfo)]),
+        "hf_query_single": (_i32, [_P, _P, _i32, ctypes.POINTER(FusedInfo)]),
+        "hf_workspace_size": (_i32, [_i32, _P, ctypes.POINTER(ctypes.c_size_t)]),
+        "hf_regcaps": (_i32, [ctypes.POINTER(_i32), _i32]),
+        "hf_device_info": (_i32, [ctypes.POINTER(DeviceLimits)]),
+        "hf_register_bound": (_i32, [ctypes.POINTER(DeviceLimits), _i32, _i32, _i32, _i32, _i32,
+                                     ctypes.POINTER(_i32)]),
+        "hf_stream_wait": (_i32, [_P, _i32]),
+        "hf_status_string": (ctypes.c_char_p, [_i32]),
+        "hf_last_error": (ctypes.c_char_p, []),
+        "hf_args_size": (ctypes.c_size_t, [_i32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def _check(fn, status):
+    if status != HF_OK:
+        raise HFError(fn, status, lib.hf_last_error().decode())
+
+
+def _stream_ptr(stream):
+    """A torch.cuda.Stream, a raw cudaStream_t int, or None (current stream)."""
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ----------------------------------------------------------------- C entry points
+def hf_register_kernel(body_id, min_threads=0, max_threads=0, granularity=0, name=None):
+    d = KernelDesc(name.encode() if name else None, body_id, min_threads, max_threads, granularity)
+    h = _P()
+    _check("hf_register_kernel", lib.hf_register_kernel(ctypes.byref(d), ctypes.byref(h)))
+    return h
+
+
+def hf_fuse(a, b, split, d0, regcap=0):
+    h = _P()
+    _check("hf_fuse", lib.hf_fuse(a, b, split, d0, regcap, ctypes.byref(h)))
+    return h
+
+
+def hf_fuse_n(kernels, interval_of, interval_threads, regcap=0):
+    n, ni = len(kernels), len(interval_threads)
+    ks = (_P * n)(*kernels)
+    io = (_i32 * n)(*interval_of)
+    it = (_i32 * ni)(*interval_threads)
+    h = _P()
+    _check("hf_fuse_n", lib.hf_fuse_n(ks, n, io, it, ni, regcap, ctypes.byref(h)))
+    return h
+
+
+def _argv(args):
+    return (_P * len(args))(*[ctypes.cast(ctypes.pointer(a), _P) for a in args])
+
+
+def hf_launch(f, args, grid=0, stream=None):
+    _check("hf_launch", lib.hf_launch(f, _argv(args), grid, _stream_ptr(stream)))
+
+
+def hf_launch_single(k, args, threads, grid=0, stream=None):
+    _check("hf_launch_single", lib.hf_launch_single(k, ctypes.cast(ctypes.pointer(args), _P),
+                                                    threads, grid, _stream_ptr(stream)))
+
+
+def hf_query(f, args):
+    info = FusedInfo()
+    _check("hf_query", lib.hf_query(f, _argv(args), ctypes.byref(info)))
+    return info.as_dict()
+
+
+def hf_query_single(k, args, threads):
+    info = FusedInfo()
+    _check("hf_query_single", lib.hf_query_single(k, ctypes.cast(ctypes.pointer(args), _P),
+                                                  threads, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def hf_workspace_size(body_id, args):
+    n = ctypes.c_size_t()
+    _check("hf_workspace_size", lib.hf_workspace_size(body_id, ctypes.cast(ctypes.pointer(args), _P),
+                                                      ctypes.byref(n)))
+    return n.value
+
+
+def hf_regcaps():
+    buf = (_i32 * 32)()
+    n = lib.hf_regcaps(buf, 32)
+    return list(buf[:n])
+
+
+def hf_device_info():
+    lim = DeviceLimits()
+    _check("hf_device_info", lib.hf_device_info(ctypes.byref(lim)))
+    return lim
+
+
+def hf_register_bound(lim, d1, nregs1, d2, nregs2, smem_fused):
+    r = _i32()
+    _check("hf_register_bound", lib.hf_register_bound(ctypes.byref(lim), d1, nregs1, d2, nregs2,
+                                                      smem_fused, ctypes.byref(r)))
+    return r.value
+
+
+def hf_stream_wait(stream=None, timeout_ms=10000):
+    _check("hf_stream_wait", lib.hf_stream_wait(_stream_ptr(stream), timeout_ms))
+
+
+def hf_destroy_fused(f):
+    lib.hf_destroy_fused(f)
+
+
+def hf_destroy_kernel(k):
+    lib.hf_destroy_kernel(k)
+
+
+# ----------------------------------------------------------------- argument blocks
+def _ptr(t):
+    return t.data_ptr() if t is not None else None
+
+
+def bn_stats_args(x, mean, var, workspace=None):
+    N, C, H, W = x.shape
+    a = BnStatsArgs(_ptr(x), _ptr(mean), _ptr(var), N, C, H * W, None)
+    if workspace is not None:
+        a.workspace = _ptr(workspace)
+    return a
+
+
+def bn_stats_workspace(x):
+    """Zero-filled device workspace for bn_stats on x (counters must start
+    at zero; every launch leaves them zero)."""
+    import torch
+    n = hf_workspace_size(BN_STATS, bn_stats_args(x, None, None))
+    return torch.zeros(max(n, 16), dtype=torch.uint8, device=x.device)
+
+
+def upsample2x_args(x, y):
+    H, W = x.shape[-2:]
+    return Upsample2xArgs(_ptr(x), _ptr(y), x.numel() // (H * W), H, W)
+
+
+def maxpool3s2_args(x, y):
+    H, W = x.shape[-2:]
+    return Maxpool3s2Args(_ptr(x), _ptr(y), x.numel() // (H * W), H, W)
+
+
+def im2col3_args(x, col):
+    N, C, H, W = x.shape
+    return Im2col3Args(_ptr(x), _ptr(col), N, C, H, W)
+
+
+def hist256_args(x, bins):
+    return Hist256Args(_ptr(x), _ptr(bins), x.numel())
+
+
+def philox_args(out, seed, first=0):
+    return PhiloxArgs(_ptr(out), out.numel() // 4, seed, first)
+
+
+def poly_args(x, y, coef, iters=64):
+    c = (_f32 * 33)(*[float(v) for v in coef])
+    return PolyArgs(_ptr(x), _ptr(y), x.numel(), iters, c)
+
+
+def bf16_axpy_args(x, y, out, alpha=0.5):
+    return Bf16AxpyArgs(_ptr(x), _ptr(y), _ptr(out), x.numel(), alpha)
+
+
+def stream_tmpl_args(x, y, k, n_barriers=0, smem_bytes=0, a=0.999, b=0.001):
+    return StreamTmplArgs(_ptr(x), _ptr(y), x.numel(), k, n_barriers, smem_bytes, a, b)

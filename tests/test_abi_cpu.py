@@ -1,0 +1,115 @@
+"""The C-ABI library on the CPU: it loads, exports every entry point that
+include/hfuse.h declares, its argument blocks match the binding, and the
+host-side validation rejects bad configurations before touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2007_01277_gb300 import build as B
+    B.build()
+    from paper_2007_01277_gb300 import hfuse
+    return hfuse
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(hf_[a-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(H):
+    names = declared_functions()
+    assert "hf_launch" in names and "hf_fuse" in names and "hf_register_kernel" in names
+    lib = ctypes.CDLL(H.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_argument_block_sizes_match(H):
+    for body, T in enumerate(H.ARGS_TYPES):
+        assert H.lib.hf_args_size(body) == ctypes.sizeof(T), H.BODY_NAMES[body]
+    assert H.lib.hf_args_size(99) == 0
+
+
+def test_status_strings(H):
+    for code in H.STATUS:
+        assert H.lib.hf_status_string(code)
+
+
+def test_register_kernel_validation(H):
+    with pytest.raises(H.HFError) as e:
+        H.hf_register_kernel(42)
+    assert e.value.status == -1
+    with pytest.raises(H.HFError):
+        H.hf_register_kernel(H.POLY, min_threads=48)
+    with pytest.raises(H.HFError):
+        H.hf_register_kernel(H.POLY, min_threads=512, max_threads=256)
+    k = H.hf_register_kernel(H.POLY, 64, 512, 64)
+    H.hf_destroy_kernel(k)
+
+
+@pytest.mark.parametrize("split,d0", [(0, 512), (512, 512), (100, 512), (256, 500), (512, 2048)])
+def test_fuse_rejects_bad_splits(H, split, d0):
+    a = H.hf_register_kernel(H.BN_STATS)
+    b = H.hf_register_kernel(H.POLY)
+    with pytest.raises(H.HFError) as e:
+        H.hf_fuse(a, b, split, d0, 0)
+    assert e.value.status == -2
+
+
+def test_fuse_respects_kernel_ranges_and_caps(H):
+    a = H.hf_register_kernel(H.HIST256, 128, 256, 128)
+    b = H.hf_register_kernel(H.PHILOX)
+    with pytest.raises(H.HFError) as e:       # 96 threads below hist's minimum
+        H.hf_fuse(a, b, 96, 512, 0)
+    assert e.value.status == -2
+    with pytest.raises(H.HFError) as e:       # 192 not a multiple of its 128 step
+        H.hf_fuse(a, b, 192, 512, 0)
+    assert e.value.status == -2
+    with pytest.raises(H.HFError) as e:
+        H.hf_fuse(a, b, 128, 512, 33)
+    assert e.value.status == -6
+
+
+def test_fuse_n_validation(H):
+    ks = [H.hf_register_kernel(H.POLY) for _ in range(3)]
+    with pytest.raises(H.HFError) as e:       # 16 intervals: only 15 barrier ids
+        H.hf_fuse_n(ks[:1] * 16, list(range(16)), [32] * 16)
+    assert e.value.status in (-3, -1)
+    with pytest.raises(H.HFError) as e:
+        H.hf_fuse_n(ks, [0, 1, 1], [512, 512, 64])          # block > 1024
+    assert e.value.status == -2
+    with pytest.raises(H.HFError) as e:
+        H.hf_fuse_n(ks, [0, 0, 0], [256, 256])              # interval 1 idle
+    assert e.value.status == -1
+
+
+def test_regcaps(H):
+    caps = H.hf_regcaps()
+    assert caps == sorted(caps) and {32, 40, 48, 64, 96} <= set(caps)
+
+
+def test_register_bound_host_arithmetic(H, orc):
+    """The library's Algorithm 2 bound agrees with the oracle's on the
+    paper's worked numbers and on a sweep."""
+    lim = H.DeviceLimits(152, 65536, 98304, 2048, 232448, 0, 10, 3)
+    assert H.hf_register_bound(lim, 896, 32, 128, 32, 1024) == 32
+    for d1 in range(128, 1024, 128):
+        for r1 in (24, 32, 40, 64, 96):
+            for r2 in (16, 32, 72):
+                for sm in (0, 1024, 40000):
+                    want = orc.register_bound(65536, 98304, 2048, d1, r1, 1024 - d1, r2, sm)
+                    assert H.hf_register_bound(lim, d1, r1, 1024 - d1, r2, sm) == want

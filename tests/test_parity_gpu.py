@@ -1,0 +1,292 @@
+"""GPU parity: every body launched alone against the FP64/exact oracle, and
+every fused launch bit-identical to its bodies launched alone with the same
+interval size and grid (the functional equivalence of Sec. 1.1 / Sec. 3.1),
+all through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+from gpu_util import (DEV, check_bf16, check_bn, check_poly, check_stream,  # noqa: E402
+                      check_upsample, single)
+from paper_2007_01277_gb300 import hfuse as H  # noqa: E402
+from paper_2007_01277_gb300 import workloads as W  # noqa: E402
+
+
+# ------------------------------------------------------------------ standalone vs oracle
+@pytest.mark.parametrize("shape", [(2, 8, 16, 12), (3, 5, 7, 9), (8, 4, 40, 40), (8, 64, 32, 32),
+                                   (1, 1, 1, 4), (5, 3, 1, 2050)])
+@pytest.mark.parametrize("threads,grid", [(256, 0), (64, 3), (1024, 1)])
+def test_bn_stats(shape, threads, grid):
+    x = W.bn_input(shape, seed=sum(shape))
+    xd = x.to(DEV)
+    C = shape[1]
+    mean = torch.empty(C, device=DEV)
+    var = torch.empty(C, device=DEV)
+    ws = H.bn_stats_workspace(xd)
+    single(H.BN_STATS, H.bn_stats_args(xd, mean, var, ws), threads, grid)
+    torch.cuda.synchronize()
+    check_bn(x, mean, var)
+    # the workspace is left clean: a second launch gives the same bits
+    m2, v2 = torch.empty_like(mean), torch.empty_like(var)
+    single(H.BN_STATS, H.bn_stats_args(xd, m2, v2, ws), threads, grid)
+    torch.cuda.synchronize()
+    assert torch.equal(mean, m2) and torch.equal(var, v2)
+
+
+def test_bn_offset_mean_and_constant_channel():
+    x = W.bn_input((4, 3, 8, 8)) * 0.01 + 1000.0
+    x[:, 1] = 7.25
+    xd = x.to(DEV)
+    mean, var = torch.empty(3, device=DEV), torch.empty(3, device=DEV)
+    single(H.BN_STATS, H.bn_stats_args(xd, mean, var, H.bn_stats_workspace(xd)), 128, 2)
+    torch.cuda.synchronize()
+    check_bn(x, mean, var)
+    assert var[1].item() == 0.0 and mean[1].item() == 7.25
+
+
+@pytest.mark.parametrize("shape", [(2, 3, 20, 24), (1, 2, 9, 7), (2, 2, 128, 128), (1, 1, 10, 260),
+                                   (1, 1, 1, 1), (3, 1, 17, 4)])
+@pytest.mark.parametrize("threads,grid", [(256, 0), (96, 5)])
+def test_upsample(shape, threads, grid):
+    x = W.upsample_input(shape, seed=sum(shape))
+    xd = x.to(DEV)
+    y = torch.empty(shape[:-2] + (2 * shape[-2], 2 * shape[-1]), device=DEV)
+    single(H.UPSAMPLE2X, H.upsample2x_args(xd, y), threads, grid)
+    torch.cuda.synchronize()
+    check_upsample(x, y)
+
+
+@pytest.mark.parametrize("shape", [(2, 3, 20, 24), (1, 2, 9, 7), (2, 4, 112, 112), (1, 1, 11, 264),
+                                   (1, 1, 1, 1), (2, 1, 2, 4)])
+@pytest.mark.parametrize("threads,grid", [(256, 0), (96, 5)])
+def test_maxpool(shape, threads, grid):
+    x = W.maxpool_input(shape, seed=sum(shape))
+    xd = x.to(DEV)
+    H_, W_ = shape[-2:]
+    y = torch.empty(shape[:-2] + ((H_ - 1) // 2 + 1, (W_ - 1) // 2 + 1), device=DEV)
+    single(H.MAXPOOL3S2, H.maxpool3s2_args(xd, y), threads, grid)
+    torch.cuda.synchronize()
+    assert np.array_equal(y.cpu().numpy(), oracle.maxpool3s2p1(x.numpy()))
+
+
+@pytest.mark.parametrize("shape", [(2, 3, 10, 12), (1, 2, 9, 7), (2, 4, 56, 56), (1, 2, 5, 68),
+                                   (1, 1, 1, 4), (2, 2, 3, 64)])
+@pytest.mark.parametrize("threads,grid", [(256, 0), (64, 7)])
+def test_im2col(shape, threads, grid):
+    x = W.im2col_input(shape, seed=sum(shape))
+    xd = x.to(DEV)
+    N, C, H_, W_ = shape
+    col = torch.full((N, C * 9, H_ * W_), float("nan"), device=DEV)
+    single(H.IM2COL3, H.im2col3_args(xd, col), threads, grid)
+    torch.cuda.synchronize()
+    assert np.array_equal(col.cpu().numpy(), oracle.im2col3(x.numpy()))
+
+
+@pytest.mark.parametrize("n,offset", [(0, 0), (1, 0), (15, 0), (16, 0), (17, 0), (1000003, 0),
+                                      (100000, 1), (5 << 20, 0)])
+@pytest.mark.parametrize("threads,grid", [(256, 0), (128, 3)])
+def test_hist(n, offset, threads, grid):
+    x = W.hist_input(n + offset, seed=n)
+    xd = x.to(DEV)[offset:]
+    bins = torch.zeros(256, dtype=torch.int32, device=DEV)
+    single(H.HIST256, H.hist256_args(xd, bins), threads, grid)
+    torch.cuda.synchronize()
+    ref = oracle.hist256(x.numpy()[offset:])
+    assert np.array_equal(bins.cpu().numpy().view(np.uint32), ref)
+
+
+@pytest.mark.parametrize("n,seed,first", [(1, 0, 0), (3, 0, 0), (1000, 0, 0),
+                                          (4097, 0x0123456789ABCDEF, 0), (300, 7, (1 << 32) - 150)])
+@pytest.mark.parametrize("threads,grid", [(256, 0), (32, 3)])
+def test_philox(n, seed, first, threads, grid):
+    out = torch.empty((n, 4), dtype=torch.int32, device=DEV)
+    single(H.PHILOX, H.philox_args(out, seed, first), threads, grid)
+    torch.cuda.synchronize()
+    ref = oracle.philox4x32_10(seed, n, first=first)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), ref)
+
+
+@pytest.mark.parametrize("n,offset,iters", [(1, 0, 64), (5, 0, 64), (4099, 0, 64), (1000, 1, 64),
+                                            (257, 0, 1), (64, 0, 0)])
+@pytest.mark.parametrize("threads,grid", [(256, 0), (64, 3)])
+def test_poly(n, offset, iters, threads, grid):
+    x = W.poly_input(n + offset, seed=n)
+    coef = W.poly_coefficients().numpy()
+    xd = x.to(DEV)[offset:]
+    y = torch.empty(n + offset, device=DEV)[offset:]
+    single(H.POLY, H.poly_args(xd, y, coef, iters), threads, grid)
+    torch.cuda.synchronize()
+    check_poly(x[offset:], coef, y, iters)
+
+
+@pytest.mark.parametrize("n,offset", [(1, 0), (9, 0), (100003, 0), (4096, 1)])
+@pytest.mark.parametrize("threads,grid", [(256, 0), (64, 3)])
+def test_bf16_axpy(n, offset, threads, grid):
+    x, y = W.bf16_inputs(n + offset, seed=n)
+    xd, yd = x.to(DEV)[offset:], y.to(DEV)[offset:]
+    out = torch.empty(n + offset, dtype=torch.bfloat16, device=DEV)[offset:]
+    single(H.BF16_AXPY, H.bf16_axpy_args(xd, yd, out, 0.5), threads, grid)
+    torch.cuda.synchronize()
+    assert check_bf16(x[offset:], y[offset:], out) == 0
+
+
+@pytest.mark.parametrize("k,nbar,smem", [(0, 0, 0), (1, 1, 0), (3, 2, 4096), (8, 4, 16384),
+                                         (65, 3, 48 * 1024), (256, 1, 0)])
+def test_stream_template(k, nbar, smem):
+    n = 4 * 1001
+    x = W.template_input(n, seed=k)
+    xd = x.to(DEV)
+    y = torch.empty_like(xd)
+    single(H.STREAM_TMPL, H.stream_tmpl_args(xd, y, k, nbar, smem, 0.999, 0.001), 128, 5)
+    torch.cuda.synchronize()
+    check_stream(x, y, k, 0.999, 0.001)
+
+
+def test_invalid_args_rejected_before_launch():
+    x = torch.zeros(8, device=DEV)
+    k = H.hf_register_kernel(H.STREAM_TMPL)
+    with pytest.raises(H.HFError) as e:                       # n not a multiple of 4
+        H.hf_launch_single(k, H.stream_tmpl_args(x[:6], x[:6], 1), 128, 1)
+    assert e.value.status == -1
+    with pytest.raises(H.HFError):                            # 50 KB staging
+        H.hf_launch_single(k, H.stream_tmpl_args(x, x, 1, 0, 50 * 1024), 128, 1)
+    kb = H.hf_register_kernel(H.BN_STATS)
+    xb = torch.zeros(1, 2, 2, 2, device=DEV)
+    m = torch.empty(2, device=DEV)
+    with pytest.raises(H.HFError):                            # no workspace
+        H.hf_launch_single(kb, H.bn_stats_args(xb, m, m, None), 128, 1)
+
+
+# ------------------------------------------------------------------ fused vs standalone
+def _case(body, seed):
+    """(args builder, outputs) for a small problem of each body."""
+    g = seed
+    if body == H.BN_STATS:
+        x = W.bn_input((4, 6, 24, 20), g).to(DEV)
+        ws = H.bn_stats_workspace(x)
+        outs = [torch.empty(6, device=DEV), torch.empty(6, device=DEV)]
+        return (lambda o: H.bn_stats_args(x, o[0], o[1], ws)), outs
+    if body == H.UPSAMPLE2X:
+        x = W.upsample_input((3, 2, 36, 40), g).to(DEV)
+        return (lambda o: H.upsample2x_args(x, o[0])), [torch.empty(3, 2, 72, 80, device=DEV)]
+    if body == H.MAXPOOL3S2:
+        x = W.maxpool_input((3, 4, 42, 40), g).to(DEV)
+        return (lambda o: H.maxpool3s2_args(x, o[0])), [torch.empty(3, 4, 21, 20, device=DEV)]
+    if body == H.IM2COL3:
+        x = W.im2col_input((2, 3, 13, 16), g).to(DEV)
+        return (lambda o: H.im2col3_args(x, o[0])), [torch.empty(2, 27, 13 * 16, device=DEV)]
+    if body == H.HIST256:
+        x = W.hist_input(300007, g).to(DEV)
+        outs = [torch.zeros(256, dtype=torch.int32, device=DEV)]
+        return (lambda o: H.hist256_args(x, o[0])), outs
+    if body == H.PHILOX:
+        return (lambda o: H.philox_args(o[0], 99, 5)), [torch.empty(5003, 4, dtype=torch.int32, device=DEV)]
+    if body == H.POLY:
+        x = W.poly_input(10007, g).to(DEV)
+        c = W.poly_coefficients().tolist()
+        return (lambda o: H.poly_args(x, o[0], c)), [torch.empty(10007, device=DEV)]
+    if body == H.BF16_AXPY:
+        x, y = (t.to(DEV) for t in W.bf16_inputs(20011, g))
+        return (lambda o: H.bf16_axpy_args(x, y, o[0])), [torch.empty(20011, dtype=torch.bfloat16, device=DEV)]
+    if body == H.STREAM_TMPL:
+        x = W.template_input(4 * 5000, g).to(DEV)
+        k = 4 + seed % 9
+        return (lambda o: H.stream_tmpl_args(x, o[0], k, 2, 2048)), [torch.empty(4 * 5000, device=DEV)]
+    raise ValueError(body)
+
+
+def _fresh(outs):
+    return [torch.zeros_like(o) for o in outs]
+
+
+PAIRS = [(H.BN_STATS, H.POLY), (H.UPSAMPLE2X, H.MAXPOOL3S2), (H.HIST256, H.PHILOX),
+         (H.STREAM_TMPL, H.STREAM_TMPL), (H.MAXPOOL3S2, H.UPSAMPLE2X), (H.BN_STATS, H.HIST256),
+         (H.IM2COL3, H.UPSAMPLE2X), (H.BF16_AXPY, H.POLY), (H.PHILOX, H.IM2COL3)]
+
+
+@pytest.mark.parametrize("pair", PAIRS, ids=lambda p: "%s+%s" % (H.BODY_NAMES[p[0]], H.BODY_NAMES[p[1]]))
+@pytest.mark.parametrize("split,d0,regcap,grid", [(256, 512, 0, 40), (128, 512, 32, 17),
+                                                   (384, 512, 64, 0), (64, 256, 0, 3)])
+def test_fused_pair_bit_exact(pair, split, d0, regcap, grid):
+    a, b = pair
+    mk_a, outs_a = _case(a, 1)
+    mk_b, outs_b = _case(b, 2)
+    ka, kb = H.hf_register_kernel(a), H.hf_register_kernel(b)
+    f = H.hf_fuse(ka, kb, split, d0, regcap)
+    fa, fb = _fresh(outs_a), _fresh(outs_b)
+    H.hf_launch(f, [mk_a(fa), mk_b(fb)], grid=grid)
+    g = grid if grid else H.hf_query(f, [mk_a(fa), mk_b(fb)])["blocks_per_sm"] * H.hf_device_info().sm_count
+    sa, sb = _fresh(outs_a), _fresh(outs_b)
+    H.hf_launch_single(ka, mk_a(sa), split, grid=g)
+    H.hf_launch_single(kb, mk_b(sb), d0 - split, grid=g)
+    torch.cuda.synchronize()
+    for u, v in zip(fa + fb, sa + sb):
+        assert torch.equal(u, v)
+    H.hf_destroy_fused(f)
+
+
+def test_fused_matches_oracle_bn_poly():
+    x = W.bn_input((8, 64, 32, 32)).to(DEV)
+    px = W.poly_input(1 << 16).to(DEV)
+    coef = W.poly_coefficients().numpy()
+    mean, var, py = torch.empty(64, device=DEV), torch.empty(64, device=DEV), torch.empty_like(px)
+    f = H.hf_fuse(H.hf_register_kernel(H.BN_STATS), H.hf_register_kernel(H.POLY), 256, 512, 0)
+    H.hf_launch(f, [H.bn_stats_args(x, mean, var, H.bn_stats_workspace(x)), H.poly_args(px, py, coef)])
+    torch.cuda.synchronize()
+    check_bn(x.cpu(), mean, var)
+    check_poly(px.cpu(), coef, py)
+
+
+def test_nway_eight_bodies_bit_exact():
+    bodies = [H.BN_STATS, H.IM2COL3, H.MAXPOOL3S2, H.UPSAMPLE2X, H.HIST256, H.PHILOX, H.POLY, H.BF16_AXPY]
+    cases = [_case(b, i + 10) for i, b in enumerate(bodies)]
+    ks = [H.hf_register_kernel(b) for b in bodies]
+    threads = [64] * 8
+    f = H.hf_fuse_n(ks, list(range(8)), threads, 0)
+    outs = [_fresh(o) for _, o in cases]
+    H.hf_launch(f, [mk(o) for (mk, _), o in zip(cases, outs)], grid=23)
+    ref = [_fresh(o) for _, o in cases]
+    for k, (mk, _), o, t in zip(ks, cases, ref, threads):
+        H.hf_launch_single(k, mk(o), t, grid=23)
+    torch.cuda.synchronize()
+    for fo, ro in zip(outs, ref):
+        for u, v in zip(fo, ro):
+            assert torch.equal(u, v)
+
+
+def test_nway_shared_interval_schedule():
+    """Several kernels on one interval run one after another (LPT-style
+    packing) and still give the bits of their standalone launches."""
+    bodies = [H.HIST256, H.STREAM_TMPL, H.BN_STATS, H.POLY, H.HIST256]
+    cases = [_case(b, i + 20) for i, b in enumerate(bodies)]
+    ks = [H.hf_register_kernel(b) for b in bodies]
+    interval_of = [0, 0, 1, 2, 1]
+    threads = [128, 256, 128]
+    f = H.hf_fuse_n(ks, interval_of, threads, 0)
+    outs = [_fresh(o) for _, o in cases]
+    H.hf_launch(f, [mk(o) for (mk, _), o in zip(cases, outs)], grid=9)
+    ref = [_fresh(o) for _, o in cases]
+    for k, (mk, _), o, i in zip(ks, cases, ref, interval_of):
+        H.hf_launch_single(k, mk(o), threads[i], grid=9)
+    torch.cuda.synchronize()
+    for fo, ro in zip(outs, ref):
+        for u, v in zip(fo, ro):
+            assert torch.equal(u, v)
+
+
+def test_stream_wait_and_query():
+    k = H.hf_register_kernel(H.POLY)
+    x = torch.rand(1 << 16, device=DEV)
+    y = torch.empty_like(x)
+    H.hf_launch_single(k, H.poly_args(x, y, [0.01] * 33), 256)
+    H.hf_stream_wait(None, 10000)
+    info = H.hf_query_single(k, H.poly_args(x, y, [0.01] * 33), 256)
+    assert info["regs"] > 0 and info["blocks_per_sm"] >= 1
+    lim = H.hf_device_info()
+    assert lim.sm_count > 0 and lim.regs_per_sm == 65536
