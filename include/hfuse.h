@@ -269,6 +269,53 @@ hf_status hf_device_info(hf_device_limits *lim);
 hf_status hf_register_bound(const hf_device_limits *lim, int d1, int nregs1,
                             int d2, int nregs2, int smem_fused, int *r0);
 
+/* ------------------------------------------------------------------ */
+/* Profiling search (Sec. 3.2).                                         */
+
+/* One timed configuration.  status is HF_OK when time_us is valid. */
+typedef struct {
+    int split;          /* threads of the first kernel (d1)            */
+    int regcap;         /* register bound, 0 = none                    */
+    int blocks_per_sm;  /* grid = blocks_per_sm * SM count             */
+    int grid;
+    float time_us;      /* median over reps                            */
+    float p10_us, p90_us;
+    int regs, spill_bytes;
+    int status;
+} hf_tune_point;
+
+/* Time a fused (or a single) launch on `stream` with CUDA events: two
+ * warm-up launches, then `reps` timed launches, each preceded by a write of
+ * a buffer twice the L2 size when flush_l2 != 0 (the buffer is allocated by
+ * the library on first use and kept).  Median and 10th/90th percentile in
+ * microseconds; outputs may be NULL.  Synchronises the stream. */
+hf_status hf_time_fused(hf_fused f, const void *const *args, int grid, int reps, int flush_l2,
+                        void *stream, float *median_us, float *p10_us, float *p90_us);
+hf_status hf_time_single(hf_kernel k, const void *args, int threads, int grid, int reps,
+                         int flush_l2, void *stream, float *median_us, float *p10_us,
+                         float *p90_us);
+
+/* Exhaustive profile of kernels a and b fused in a d0-thread block over
+ * every (split, regcap, blocks_per_sm) of the given lists; table receives
+ * n_splits * n_regcaps * n_bps points in that nesting order.  Points that
+ * cannot be built or are not resident carry a non-OK status and time -1.
+ * Note: kernels that accumulate into their outputs (the histogram) run
+ * (reps + 2) times per point. */
+hf_status hf_profile_pair(hf_kernel a, hf_kernel b, const void *const *args, int d0,
+                          const int *splits, int n_splits, const int *regcaps, int n_regcaps,
+                          const int *bps, int n_bps, int reps, int flush_l2, void *stream,
+                          hf_tune_point *table);
+
+/* Algorithm 2 (Sec. 3.2): for d1 = step, 2*step, ... < d0 profile the fused
+ * kernel without a register bound and with the bound r0 of
+ * hf_register_bound (NRegs from the kernels compiled alone at d1 and
+ * d0 - d1, ShMem from the fused instance), r0 snapped down to the nearest
+ * compiled cap; keep the first strictly fastest.  Grid = resident blocks per
+ * SM * SM count.  The visited points go to trace (up to trace_cap). */
+hf_status hf_search_alg2(hf_kernel a, hf_kernel b, const void *const *args, int d0, int step,
+                         int reps, int flush_l2, void *stream, hf_tune_point *best,
+                         hf_tune_point *trace, int trace_cap, int *n_trace);
+
 /* Waits until all work queued on `stream` has finished, polling for at most
  * timeout_ms milliseconds: HF_ERR_TIMEOUT if it has not finished by then
  * (the work keeps running; nothing is cancelled), HF_ERR_CUDA if the stream

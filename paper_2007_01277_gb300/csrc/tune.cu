@@ -1,0 +1,221 @@
+// tune.cu -- profiling search over fusion configurations (Sec. 3.2).
+//
+// hf_time_fused / hf_time_single time one configuration with CUDA events on
+// the caller's stream: two warm-up launches, then `reps` launches each
+// preceded (optionally) by a write of a buffer twice the L2 size, median and
+// 10th/90th percentiles.  hf_profile_pair times the whole grid of (split,
+// register cap, blocks/SM) points -- the exhaustive search and the training
+// data of the cost model.  hf_search_alg2 is Algorithm 2: d1 = step, 2 step,
+// ... < d0, each profiled without a bound and with the bound r0 of the
+// register-bound formula (snapped down to the nearest compiled cap), keeping
+// the first strictly faster configuration.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "kernels.cuh"
+
+extern "C" {
+hf_status hf_query_single(hf_kernel k, const void *args, int threads, hf_fused_info *info);
+}
+
+namespace {
+
+struct FlushBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+std::mutex g_flush_mu;
+FlushBuf g_flush;
+
+hf_status flush_l2(cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(g_flush_mu);
+    if (!g_flush.ptr) {
+        int dev = 0, l2 = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return HF_ERR_CUDA;
+        if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) return HF_ERR_CUDA;
+        g_flush.bytes = 2 * (size_t)std::max(l2, 1 << 20);
+        if (cudaMalloc(&g_flush.ptr, g_flush.bytes) != cudaSuccess) {
+            g_flush.ptr = nullptr;
+            return HF_ERR_CUDA;
+        }
+    }
+    return cudaMemsetAsync(g_flush.ptr, 0, g_flush.bytes, s) == cudaSuccess ? HF_OK : HF_ERR_CUDA;
+}
+
+template <class F>
+hf_status time_it(F launch, int reps, int flush, cudaStream_t s, float *med, float *p10, float *p90)
+{
+    if (reps < 1) return HF_ERR_INVALID;
+    for (int w = 0; w < 2; ++w) {
+        hf_status st = launch();
+        if (st) return st;
+    }
+    std::vector<cudaEvent_t> ev(2 * reps);
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return HF_ERR_CUDA;
+    hf_status st = HF_OK;
+    for (int r = 0; r < reps && !st; ++r) {
+        if (flush) st = flush_l2(s);
+        if (st) break;
+        cudaEventRecord(ev[2 * r], s);
+        st = launch();
+        cudaEventRecord(ev[2 * r + 1], s);
+    }
+    std::vector<float> t;
+    if (!st && cudaStreamSynchronize(s) != cudaSuccess) st = HF_ERR_CUDA;
+    if (!st)
+        for (int r = 0; r < reps; ++r) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]);
+            t.push_back(ms * 1000.f);
+        }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (st) return st;
+    std::sort(t.begin(), t.end());
+    auto q = [&](double f) { return t[std::min((size_t)(f * (t.size() - 1) + 0.5), t.size() - 1)]; };
+    if (med) *med = q(0.5);
+    if (p10) *p10 = q(0.1);
+    if (p90) *p90 = q(0.9);
+    return HF_OK;
+}
+
+int snap_cap(int r0)
+{
+    int caps[32];
+    const int n = hf_regcaps(caps, 32);
+    int best = 0;
+    for (int i = 0; i < n && i < 32; ++i)
+        if (caps[i] <= r0) best = caps[i];
+    return best;
+}
+
+} // namespace
+
+extern "C" {
+
+hf_status hf_time_fused(hf_fused f, const void *const *args, int grid, int reps, int flush_l2_,
+                        void *stream, float *median_us, float *p10_us, float *p90_us)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return time_it([&] { return hf_launch(f, args, grid, stream); }, reps, flush_l2_, s, median_us,
+                   p10_us, p90_us);
+}
+
+hf_status hf_time_single(hf_kernel k, const void *args, int threads, int grid, int reps,
+                         int flush_l2_, void *stream, float *median_us, float *p10_us, float *p90_us)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return time_it([&] { return hf_launch_single(k, args, threads, grid, stream); }, reps, flush_l2_,
+                   s, median_us, p10_us, p90_us);
+}
+
+hf_status hf_profile_pair(hf_kernel a, hf_kernel b, const void *const *args, int d0, const int *splits,
+                          int n_splits, const int *regcaps, int n_regcaps, const int *bps, int n_bps,
+                          int reps, int flush_l2_, void *stream, hf_tune_point *table)
+{
+    if (!a || !b || !args || !splits || !regcaps || !bps || !table || n_splits < 1 || n_regcaps < 1 ||
+        n_bps < 1)
+        return HF_ERR_INVALID;
+    hf_device_limits lim;
+    hf_status st = hf_device_info(&lim);
+    if (st) return st;
+    int idx = 0;
+    for (int i = 0; i < n_splits; ++i)
+        for (int j = 0; j < n_regcaps; ++j) {
+            hf_fused f = nullptr;
+            hf_status fs = hf_fuse(a, b, splits[i], d0, regcaps[j], &f);
+            hf_fused_info info;
+            std::memset(&info, 0, sizeof info);
+            if (!fs) fs = hf_query(f, args, &info);
+            for (int k = 0; k < n_bps; ++k, ++idx) {
+                hf_tune_point &p = table[idx];
+                std::memset(&p, 0, sizeof p);
+                p.split = splits[i];
+                p.regcap = regcaps[j];
+                p.blocks_per_sm = bps[k];
+                p.regs = info.regs;
+                p.spill_bytes = info.spill_bytes;
+                p.status = fs;
+                p.time_us = -1.f;
+                if (fs) continue;
+                if (bps[k] < 1 || bps[k] > info.blocks_per_sm) {
+                    p.status = HF_ERR_REGS;   // not resident at this many blocks per SM
+                    continue;
+                }
+                p.grid = bps[k] * lim.sm_count;
+                p.status = hf_time_fused(f, args, p.grid, reps, flush_l2_, stream, &p.time_us,
+                                         &p.p10_us, &p.p90_us);
+                if (p.status == HF_ERR_CUDA) {
+                    hf_destroy_fused(f);
+                    return HF_ERR_CUDA;
+                }
+            }
+            if (f) hf_destroy_fused(f);
+        }
+    return HF_OK;
+}
+
+hf_status hf_search_alg2(hf_kernel a, hf_kernel b, const void *const *args, int d0, int step,
+                         int reps, int flush_l2_, void *stream, hf_tune_point *best,
+                         hf_tune_point *trace, int trace_cap, int *n_trace)
+{
+    if (!a || !b || !args || !best || step < 32 || step % 32) return HF_ERR_INVALID;
+    hf_device_limits lim;
+    hf_status st = hf_device_info(&lim);
+    if (st) return st;
+    std::memset(best, 0, sizeof *best);
+    best->time_us = -1.f;
+    int nt = 0;
+    auto record = [&](const hf_tune_point &p) {
+        if (trace && nt < trace_cap) trace[nt] = p;
+        ++nt;
+    };
+    for (int d1 = step; d1 < d0; d1 += step) {
+        const int d2 = d0 - d1;
+        // NRegs(S1), NRegs(S2): the kernels compiled alone
+        hf_fused_info ia, ib;
+        if (hf_query_single(a, args[0], d1, &ia) || hf_query_single(b, args[1], d2, &ib)) continue;
+        for (int pass = 0; pass < 2; ++pass) {
+            hf_fused f = nullptr;
+            int cap = 0;
+            hf_fused_info info;
+            if (pass == 1) {
+                // ShMem(F) of the unbounded instance, then the bound r0
+                hf_fused f0 = nullptr;
+                if (hf_fuse(a, b, d1, d0, 0, &f0)) continue;
+                hf_status qs = hf_query(f0, args, &info);
+                hf_destroy_fused(f0);
+                if (qs) continue;
+                int r0 = 0;
+                hf_register_bound(&lim, d1, ia.regs, d2, ib.regs, info.smem_bytes, &r0);
+                cap = snap_cap(r0);
+                if (cap == 0) continue;   // no compiled cap at or below r0
+            }
+            if (hf_fuse(a, b, d1, d0, cap, &f)) continue;
+            hf_tune_point p;
+            std::memset(&p, 0, sizeof p);
+            p.split = d1;
+            p.regcap = cap;
+            p.status = hf_query(f, args, &info);
+            if (!p.status) {
+                p.regs = info.regs;
+                p.spill_bytes = info.spill_bytes;
+                p.blocks_per_sm = info.blocks_per_sm;
+                p.grid = info.blocks_per_sm * lim.sm_count;
+                p.status = hf_time_fused(f, args, p.grid, reps, flush_l2_, stream, &p.time_us,
+                                         &p.p10_us, &p.p90_us);
+            }
+            hf_destroy_fused(f);
+            if (p.status == HF_ERR_CUDA) return HF_ERR_CUDA;
+            record(p);
+            if (!p.status && (best->time_us < 0.f || p.time_us < best->time_us)) *best = p;
+        }
+    }
+    if (n_trace) *n_trace = nt;
+    return best->time_us < 0.f ? HF_ERR_INVALID : HF_OK;
+}
+
+} // extern "C"

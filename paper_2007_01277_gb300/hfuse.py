@@ -92,6 +92,15 @@ class DeviceLimits(ctypes.Structure):
                 ("cc_major", _i32), ("cc_minor", _i32)]
 
 
+class TunePoint(ctypes.Structure):
+    _fields_ = [("split", _i32), ("regcap", _i32), ("blocks_per_sm", _i32), ("grid", _i32),
+                ("time_us", _f32), ("p10_us", _f32), ("p90_us", _f32), ("regs", _i32),
+                ("spill_bytes", _i32), ("status", _i32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class HFError(RuntimeError):
     def __init__(self, fn, status, msg):
         super().__init__("%s -> %s: %s" % (fn, STATUS.get(status, status), msg))
@@ -121,6 +130,16 @@ def _load():
         "hf_register_bound": (_i32, [ctypes.POINTER(DeviceLimits), _i32, _i32, _i32, _i32, _i32,
                                      ctypes.POINTER(_i32)]),
         "hf_stream_wait": (_i32, [_P, _i32]),
+        "hf_time_fused": (_i32, [_P, ctypes.POINTER(_P), _i32, _i32, _i32, _P,
+                                 ctypes.POINTER(_f32), ctypes.POINTER(_f32), ctypes.POINTER(_f32)]),
+        "hf_time_single": (_i32, [_P, _P, _i32, _i32, _i32, _i32, _P, ctypes.POINTER(_f32),
+                                  ctypes.POINTER(_f32), ctypes.POINTER(_f32)]),
+        "hf_profile_pair": (_i32, [_P, _P, ctypes.POINTER(_P), _i32, ctypes.POINTER(_i32), _i32,
+                                   ctypes.POINTER(_i32), _i32, ctypes.POINTER(_i32), _i32, _i32,
+                                   _i32, _P, ctypes.POINTER(TunePoint)]),
+        "hf_search_alg2": (_i32, [_P, _P, ctypes.POINTER(_P), _i32, _i32, _i32, _i32, _P,
+                                  ctypes.POINTER(TunePoint), ctypes.POINTER(TunePoint), _i32,
+                                  ctypes.POINTER(_i32)]),
         "hf_status_string": (ctypes.c_char_p, [_i32]),
         "hf_last_error": (ctypes.c_char_p, []),
         "hf_args_size": (ctypes.c_size_t, [_i32]),
@@ -293,3 +312,40 @@ def bf16_axpy_args(x, y, out, alpha=0.5):
 
 def stream_tmpl_args(x, y, k, n_barriers=0, smem_bytes=0, a=0.999, b=0.001):
     return StreamTmplArgs(_ptr(x), _ptr(y), x.numel(), k, n_barriers, smem_bytes, a, b)
+
+
+# ----------------------------------------------------------------- profiling search
+def hf_time_fused(f, args, grid=0, reps=10, flush_l2=True, stream=None):
+    m, lo, hi = _f32(), _f32(), _f32()
+    _check("hf_time_fused", lib.hf_time_fused(f, _argv(args), grid, reps, int(flush_l2),
+                                              _stream_ptr(stream), ctypes.byref(m), ctypes.byref(lo),
+                                              ctypes.byref(hi)))
+    return m.value, lo.value, hi.value
+
+
+def hf_time_single(k, args, threads, grid=0, reps=10, flush_l2=True, stream=None):
+    m, lo, hi = _f32(), _f32(), _f32()
+    _check("hf_time_single", lib.hf_time_single(k, ctypes.cast(ctypes.pointer(args), _P), threads,
+                                                grid, reps, int(flush_l2), _stream_ptr(stream),
+                                                ctypes.byref(m), ctypes.byref(lo), ctypes.byref(hi)))
+    return m.value, lo.value, hi.value
+
+
+def hf_profile_pair(a, b, args, d0, splits, regcaps, bps, reps=5, flush_l2=True, stream=None):
+    n = len(splits) * len(regcaps) * len(bps)
+    table = (TunePoint * n)()
+    _check("hf_profile_pair", lib.hf_profile_pair(
+        a, b, _argv(args), d0, (_i32 * len(splits))(*splits), len(splits),
+        (_i32 * len(regcaps))(*regcaps), len(regcaps), (_i32 * len(bps))(*bps), len(bps), reps,
+        int(flush_l2), _stream_ptr(stream), table))
+    return [p.as_dict() for p in table]
+
+
+def hf_search_alg2(a, b, args, d0, step=128, reps=5, flush_l2=True, stream=None):
+    best = TunePoint()
+    trace = (TunePoint * 64)()
+    nt = _i32()
+    _check("hf_search_alg2", lib.hf_search_alg2(a, b, _argv(args), d0, step, reps, int(flush_l2),
+                                                _stream_ptr(stream), ctypes.byref(best), trace, 64,
+                                                ctypes.byref(nt)))
+    return best.as_dict(), [trace[i].as_dict() for i in range(min(nt.value, 64))]
