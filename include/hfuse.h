@@ -316,6 +316,35 @@ hf_status hf_search_alg2(hf_kernel a, hf_kernel b, const void *const *args, int 
                          int reps, int flush_l2, void *stream, hf_tune_point *best,
                          hf_tune_point *trace, int trace_cap, int *n_trace);
 
+/* ------------------------------------------------------------------ */
+/* Allocation-free batch-norm statistics.                               */
+
+/* Size of the fixed device scratch array behind hf_bn_stats_noalloc: room
+ * for the per-channel counters (4 bytes each, rounded up to 256 bytes) and
+ * one 8-byte partial sum per 2048-value tile of every channel, i.e. up to
+ * about 129,000 tiles (264 million input values) at C <= 4096. */
+#define HF_BN_NOALLOC_SCRATCH_BYTES (1 << 20)
+
+/* Batch-norm statistics (same result as HF_BODY_BN_STATS launched alone with
+ * the same threads and grid) that allocates no device memory.  It is meant
+ * for callers that must not call cudaMalloc: hosts whose device memory is
+ * fully reserved up front, or latency-bound loops where an allocation would
+ * stall every stream.  It has no counterpart in the paper.
+ *
+ * Instead of a caller workspace it uses one file-scope device array of
+ * HF_BN_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds
+ * until the process exits.  The first call on a device looks up that
+ * array's device address (once, with the device current); make that first
+ * call before any stream capture.  Every call clears the counters at the
+ * start of the array on `stream` and then launches; calls share the one
+ * array, so calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  Shapes whose scratch
+ * would exceed the array are rejected with HF_ERR_INVALID before anything
+ * is queued.  grid = 0 picks resident blocks per SM times the SM count.
+ * x is float32 [N][C][HW]; mean and var receive C floats. */
+hf_status hf_bn_stats_noalloc(const float *x, float *mean, float *var, int N, int C, int HW,
+                              int threads, int grid, void *stream);
+
 /* Waits until all work queued on `stream` has finished, polling for at most
  * timeout_ms milliseconds: HF_ERR_TIMEOUT if it has not finished by then
  * (the work keeps running; nothing is cancelled), HF_ERR_CUDA if the stream

@@ -310,6 +310,11 @@ hf_status nway_params(const hf_fused_t *f, const void *const *args, NwayParams *
 }
 } // namespace
 
+// Records a one-line error for hf_last_error() from other translation units.
+namespace hf {
+hf_status set_last_error(hf_status s, const char *msg) { return fail(s, "%s", msg); }
+} // namespace hf
+
 // ------------------------------------------------------------------ C ABI
 extern "C" {
 

@@ -140,6 +140,7 @@ def _load():
         "hf_search_alg2": (_i32, [_P, _P, ctypes.POINTER(_P), _i32, _i32, _i32, _i32, _P,
                                   ctypes.POINTER(TunePoint), ctypes.POINTER(TunePoint), _i32,
                                   ctypes.POINTER(_i32)]),
+        "hf_bn_stats_noalloc": (_i32, [_P, _P, _P, _i32, _i32, _i32, _i32, _i32, _P]),
         "hf_status_string": (ctypes.c_char_p, [_i32]),
         "hf_last_error": (ctypes.c_char_p, []),
         "hf_args_size": (ctypes.c_size_t, [_i32]),
@@ -349,3 +350,12 @@ def hf_search_alg2(a, b, args, d0, step=128, reps=5, flush_l2=True, stream=None)
                                                 _stream_ptr(stream), ctypes.byref(best), trace, 64,
                                                 ctypes.byref(nt)))
     return best.as_dict(), [trace[i].as_dict() for i in range(min(nt.value, 64))]
+
+
+# ----------------------------------------------------------------- allocation-free entry point
+def hf_bn_stats_noalloc(x, mean, var, threads=256, grid=0, stream=None):
+    """Batch-norm statistics through the entry point that allocates nothing
+    (its scratch is a fixed device array inside the library)."""
+    N, C, Hh, Ww = x.shape
+    _check("hf_bn_stats_noalloc", lib.hf_bn_stats_noalloc(
+        _ptr(x), _ptr(mean), _ptr(var), N, C, Hh * Ww, threads, grid, _stream_ptr(stream)))
