@@ -48,218 +48,470 @@ def algorithmic_bytes():
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    """Samples nvidia-smi during the timed region (200 ms period)."""
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """Samples the SM clock and the clock-event reasons every millisecond
+    while the timed region runs, through read-only NVML queries (ctypes on
+    libnvidia-ml); nvidia-smi at 50 ms if NVML cannot be loaded."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, index: int):
-        self.index = index
+    def __init__(self, torch_device):
+        self.dev = torch_device
+        self.samples = []
+        self.max_mhz = None
+        self.reasons = set()
+        self.stop = threading.Event()
+        self.nvml = None
         self.proc = None
-        self.lines = []
+
+    def _open_nvml(self):
+        import ctypes
+        import torch
+        L = ctypes.CDLL("libnvidia-ml.so.1")
+        if L.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        pr = torch.cuda.get_device_properties(self.dev)
+        bus = "%08X:%02X:%02X.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        if L.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) != 0:
+            raise OSError("no NVML handle for " + bus)
+        self.L, self.h, self.ct = L, h, ctypes
+        m = ctypes.c_uint()
+        if L.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(m)) == 0:
+            self.max_mhz = float(m.value)
+        self.nvml = True
+
+    def _poll_nvml(self):
+        c, r = self.ct.c_uint(), self.ct.c_ulonglong()
+        get_r = getattr(self.L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.L.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop.is_set():
+            if self.L.nvmlDeviceGetClockInfo(self.h, 1, self.ct.byref(c)) == 0:
+                self.samples.append(float(c.value))
+            if get_r(self.h, self.ct.byref(r)) == 0:
+                for bit, name in self.REASONS.items():
+                    if r.value & bit:
+                        self.reasons.add(name)
+            time.sleep(0.001)
+
+    def _poll_smi(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            try:
+                self.samples.append(float(parts[0]))
+                self.max_mhz = float(parts[1])
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                              "sw_power_cap"], parts[2:6]):
+                if v.lower() == "active":
+                    self.reasons.add(nm)
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+            self._open_nvml()
+            self.t = threading.Thread(target=self._poll_nvml, daemon=True)
         except OSError:
-            self.proc = None
+            import torch
+            idx = os.environ.get("CUDA_VISIBLE_DEVICES", str(torch.cuda.current_device())).split(",")[0]
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", idx, "--query-gpu=clocks.sm,clocks.max.sm,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._poll_smi, daemon=True)
+        self.t.start()
+        time.sleep(0.005)
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
-
     def __exit__(self, *exc):
+        self.stop.set()
         if self.proc is not None:
             self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
+        self.t.join(timeout=5)
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 8:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                mx = float(parts[1])
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[4:8]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        s = self.samples
+        return {"sm_mhz": statistics.median(s) if s else None, "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(self.reasons), "samples": len(s),
+                "source": "nvml" if self.nvml else "nvidia-smi"}
 
 
-# ------------------------------------------------------------------ our arm
-def run_ours(args):
+# ------------------------------------------------------------------ workloads
+def _mb(n):
+    return n / 1e6
+
+
+PAIR_SPECS = {
+    # bilinear x2 of 32x64x128x128 + 3x3/s2/p1 max pool of 32x128x112x112
+    "upsample_maxpool": dict(d0=512, splits=(128, 256, 384), caps=(0, 64, 96), bps=(1, 2, 3),
+                             flush=False, name="fused_upsample_maxpool",
+                             desc=WORKLOAD),
+    # 2^28-byte histogram + 2^26 Philox4x32-10 blocks
+    "hist_philox": dict(d0=256, splits=tuple(range(32, 256, 32)), caps=(0, 32, 40, 48, 64, 96),
+                        bps=(1, 2, 3, 4), flush=False, name="fused_hist_philox",
+                        desc="hist256 of 2^28 u8 ~U[0,255] + Philox4x32-10 producing 2^26 blocks "
+                             "(seed 0), fused in one launch"),
+    # batch-norm stats of 8x64x32x32 + 64-step degree-32 Horner chain on 2^20
+    "bn_poly": dict(d0=512, splits=(128, 256, 384), caps=(0, 32, 40, 48, 64, 96), bps=(1, 2, 3, 4),
+                    flush=True, name="fused_bn_poly",
+                    desc="bn stats FP32 8x64x32x32 ~N(0,1) + 64x degree-32 Horner on 2^20 FP32 "
+                         "~U(-1,1), fused in one launch"),
+}
+
+
+def make_pair(name, H, W, dev):
+    """(body ids, arg blocks, tensors, algorithmic bytes, pipe ops, host inputs, outputs)."""
     import torch
+    if name == "upsample_maxpool":
+        xu_h = W.upsample_input(UP_SHAPE).pin_memory()
+        xp_h = W.maxpool_input(POOL_SHAPE).pin_memory()
+        xu, xp = xu_h.to(dev), xp_h.to(dev)
+        yu = torch.empty(UP_SHAPE[:2] + (256, 256), device=dev)
+        yp = torch.empty(POOL_SHAPE[:2] + (56, 56), device=dev)
+        return ((H.UPSAMPLE2X, H.MAXPOOL3S2), [H.upsample2x_args(xu, yu), H.maxpool3s2_args(xp, yp)],
+                algorithmic_bytes(), {}, [(xu_h, xu), (xp_h, xp)], [yu, yp])
+    if name == "hist_philox":
+        xh_h = W.hist_input(1 << 28).pin_memory()
+        xh = xh_h.to(dev)
+        bins = torch.zeros(256, dtype=torch.int32, device=dev)
+        out = torch.empty((1 << 26, 4), dtype=torch.int32, device=dev)
+        nbytes = (1 << 28) + 256 * 4 + (1 << 26) * 16
+        ops = {"imul": (1 << 26) * 40, "smem_atomic": 1 << 28}
+        return ((H.HIST256, H.PHILOX), [H.hist256_args(xh, bins), H.philox_args(out, 0)], nbytes, ops,
+                [(xh_h, xh)], [bins, out])
+    if name == "bn_poly":
+        xb_h = W.bn_input((8, 64, 32, 32)).pin_memory()
+        xq_h = W.poly_input(1 << 20).pin_memory()
+        xb, xq = xb_h.to(dev), xq_h.to(dev)
+        m, v = torch.empty(64, device=dev), torch.empty(64, device=dev)
+        yq = torch.empty_like(xq)
+        ws = H.bn_stats_workspace(xb)
+        nbytes = xb.numel() * 4 + 2 * 64 * 4 + 2 * xq.numel() * 4
+        ops = {"ffma": (1 << 20) * 64 * 33 + 2 * xb.numel()}
+        return ((H.BN_STATS, H.POLY), [H.bn_stats_args(xb, m, v, ws),
+                                       H.poly_args(xq, yq, W.poly_coefficients().tolist())],
+                nbytes, ops, [(xb_h, xb), (xq_h, xq)], [m, v, yq, ws])
+    raise SystemExit("unknown pair workload " + name)
 
-    from paper_2007_01277_gb300 import hfuse as H
-    from paper_2007_01277_gb300 import workloads as W
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+def pipe_peaks(H, stream):
+    return {"ffma": H.hf_calibrate(H.CAL_FFMA, stream), "imul": H.hf_calibrate(H.CAL_IMUL, stream),
+            "smem_atomic": H.hf_calibrate(H.CAL_SMEM_ATOMIC, stream)}
 
-    x_up_h = W.upsample_input(UP_SHAPE).pin_memory()
-    x_pool_h = W.maxpool_input(POOL_SHAPE).pin_memory()
-    x_up = x_up_h.to(dev)
-    x_pool = x_pool_h.to(dev)
-    y_up = torch.empty(UP_SHAPE[:2] + (256, 256), device=dev)
-    y_pool = torch.empty(POOL_SHAPE[:2] + (56, 56), device=dev)
-    a_up = H.upsample2x_args(x_up, y_up)
-    a_pool = H.maxpool3s2_args(x_pool, y_pool)
-    k_up = H.hf_register_kernel(H.UPSAMPLE2X)
-    k_pool = H.hf_register_kernel(H.MAXPOOL3S2)
-    lim = H.hf_device_info()
-    stream = torch.cuda.Stream(device=dev)
-    s2 = torch.cuda.Stream(device=dev)
 
-    def timed(fn, reps, warm=2):
-        with torch.cuda.stream(stream):
+def ideal_us(nbytes, ops, peaks, hbm_gbs):
+    terms = {"hbm": nbytes / (hbm_gbs * 1e9) * 1e6}
+    for k, v in ops.items():
+        terms[k] = v / peaks[k] * 1e6
+    return max(terms.values()), {k: round(v, 2) for k, v in terms.items()}
+
+
+class Ctx:
+    """Per-run state: device, streams, distributed group, timing helpers."""
+
+    def __init__(self, args):
+        import torch
+        self.torch = torch
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        self.dev = torch.device("cuda", local)
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl")
+            self.dist = dist
+        self.stream = torch.cuda.Stream(device=self.dev)
+        self.flush_buf = None
+        self.args = args
+
+    def flush(self):
+        if self.flush_buf is None:
+            self.flush_buf = self.torch.empty(512 << 20, dtype=self.torch.uint8, device=self.dev)
+        self.flush_buf.zero_()
+
+    def timed(self, fn, reps, warm=2, flush=False):
+        torch = self.torch
+        s = self.stream
+        with torch.cuda.stream(s):
             for _ in range(warm):
                 fn()
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
             for i in range(reps):
-                ev[2 * i].record(stream)
+                if flush:
+                    self.flush()
+                ev[2 * i].record(s)
                 fn()
-                ev[2 * i + 1].record(stream)
+                ev[2 * i + 1].record(s)
             torch.cuda.synchronize()
         return [ev[2 * i].elapsed_time(ev[2 * i + 1]) * 1e3 for i in range(reps)]
 
-    # --- configuration sweep (outside the timed region)
-    best = None
-    sweep = []
-    for split in (128, 256, 384):
-        for cap in (0, 64, 96):
-            f = H.hf_fuse(k_up, k_pool, split, 512, cap)
-            info = H.hf_query(f, [a_up, a_pool])
-            for bps in sorted({1, info["blocks_per_sm"]}):
-                grid = bps * lim.sm_count
-                t = statistics.median(timed(lambda: H.hf_launch(f, [a_up, a_pool], grid, stream), 5))
-                sweep.append({"split": split, "regcap": cap, "grid": grid, "us": round(t, 2),
-                              "regs": info["regs"], "spill": info["spill_bytes"]})
-                if best is None or t < best[0]:
-                    best = (t, split, cap, grid)
-            H.hf_destroy_fused(f)
-    _, split, cap, grid = best
-    fused = H.hf_fuse(k_up, k_pool, split, 512, cap)
+    def barrier(self):
+        if self.dist:
+            self.dist.barrier()
+        self.torch.cuda.synchronize()
 
-    # standalone configurations: best threads for each kernel alone
+    def max_over_ranks(self, v):
+        if not self.dist:
+            return v
+        t = self.torch.tensor([v], device=self.dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return t.item()
+
+
+def run_pair(cx, name):
+    import torch
+
+    from paper_2007_01277_gb300 import hfuse as H
+    from paper_2007_01277_gb300 import workloads as W
+    spec = PAIR_SPECS[name]
+    bodies, args, nbytes, ops, host_in, outs = make_pair(name, H, W, cx.dev)
+    ka, kb = H.hf_register_kernel(bodies[0]), H.hf_register_kernel(bodies[1])
+    lim = H.hf_device_info()
+    st, d0, fl = cx.stream, spec["d0"], spec["flush"]
+
+    # exhaustive search over (split, regcap, blocks/SM) -- outside the timed region
+    table = H.hf_profile_pair(ka, kb, args, d0, list(spec["splits"]), list(spec["caps"]),
+                              list(spec["bps"]), reps=5, flush_l2=fl, stream=st)
+    ok = [p for p in table if p["status"] == 0]
+    best = min(ok, key=lambda p: p["time_us"])
+    alg2, _trace = H.hf_search_alg2(ka, kb, args, d0, step=128 if d0 >= 512 else 64, reps=5,
+                                    flush_l2=fl, stream=st)
+    naive = [p for p in ok if p["split"] == d0 // 2 and p["regcap"] == 0]
+    naive = min(naive, key=lambda p: -p["blocks_per_sm"]) if naive else None
+    fused = H.hf_fuse(ka, kb, best["split"], d0, best["regcap"])
+    grid = best["grid"]
+
     def best_single(k, a):
         res = []
         for thr in (128, 256, 512):
             info = H.hf_query_single(k, a, thr)
             g = info["blocks_per_sm"] * lim.sm_count
-            t = statistics.median(timed(lambda: H.hf_launch_single(k, a, thr, g, stream), 5))
+            t = statistics.median(cx.timed(lambda: H.hf_launch_single(k, a, thr, g, st), 5, flush=fl))
             res.append((t, thr, g))
         return min(res)
 
-    t_up, thr_up, g_up = best_single(k_up, a_up)
-    t_pool, thr_pool, g_pool = best_single(k_pool, a_pool)
+    ta, thr_a, g_a = best_single(ka, args[0])
+    tb, thr_b, g_b = best_single(kb, args[1])
+    s2 = torch.cuda.Stream(device=cx.dev)
+    ev_f, ev_j = torch.cuda.Event(), torch.cuda.Event()
 
     def step_fused():
-        H.hf_launch(fused, [a_up, a_pool], grid, stream)
+        H.hf_launch(fused, args, grid, st)
 
     def step_serial():
-        H.hf_launch_single(k_up, a_up, thr_up, g_up, stream)
-        H.hf_launch_single(k_pool, a_pool, thr_pool, g_pool, stream)
+        H.hf_launch_single(ka, args[0], thr_a, g_a, st)
+        H.hf_launch_single(kb, args[1], thr_b, g_b, st)
 
-    ev_fork = torch.cuda.Event()
-    ev_join = torch.cuda.Event()
+    def step_two():
+        ev_f.record(st)
+        s2.wait_event(ev_f)
+        H.hf_launch_single(ka, args[0], thr_a, g_a, st)
+        H.hf_launch_single(kb, args[1], thr_b, g_b, s2)
+        ev_j.record(s2)
+        st.wait_event(ev_j)
 
-    def step_two_stream():
-        ev_fork.record(stream)
-        s2.wait_event(ev_fork)
-        H.hf_launch_single(k_up, a_up, thr_up, g_up, stream)
-        H.hf_launch_single(k_pool, a_pool, thr_pool, g_pool, s2)
-        ev_join.record(s2)
-        stream.wait_event(ev_join)
+    K, Wm = cx.args.steps, cx.args.warmup
+    cx.barrier()
+    with ClockSampler(cx.dev) as clk:
+        per = cx.timed(step_fused, K, warm=Wm, flush=fl)
+    cx.barrier()
+    t_fused = cx.max_over_ranks(statistics.mean(per))
+    t_serial = statistics.median(cx.timed(step_serial, max(5, K // 4), warm=Wm, flush=fl))
+    t_two = statistics.median(cx.timed(step_two, max(5, K // 4), warm=Wm, flush=fl))
 
-    W_, K = args.warmup, args.steps
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        per_launch = timed(step_fused, K, warm=W_)
-    clocks = clk.summary()
-    t_fused = statistics.mean(per_launch)
-    t_serial = statistics.median(timed(step_serial, max(5, K // 2), warm=W_))
-    t_two = statistics.median(timed(step_two_stream, max(5, K // 2), warm=W_))
-
-    # whole-region time, max over ranks
-    if dist:
-        tt = torch.tensor([t_fused], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_fused = tt.item()
-
-    # --- end to end: host buffers in, fused launch, host buffers out
-    y_up_h = torch.empty(y_up.shape, pin_memory=True)
-    y_pool_h = torch.empty(y_pool.shape, pin_memory=True)
+    host_out = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs]
 
     def step_e2e():
-        x_up.copy_(x_up_h, non_blocking=True)
-        x_pool.copy_(x_pool_h, non_blocking=True)
-        H.hf_launch(fused, [a_up, a_pool], grid, stream)
-        y_up_h.copy_(y_up, non_blocking=True)
-        y_pool_h.copy_(y_pool, non_blocking=True)
+        for h, d in host_in:
+            d.copy_(h, non_blocking=True)
+        H.hf_launch(fused, args, grid, st)
+        for h, d in zip(host_out, outs):
+            h.copy_(d, non_blocking=True)
 
-    t_e2e = statistics.median(timed(step_e2e, max(3, K // 4), warm=1))
-    h2d = (x_up.numel() + x_pool.numel()) * 4
-    d2h = (y_up.numel() + y_pool.numel()) * 4
+    t_e2e = statistics.median(cx.timed(step_e2e, max(3, K // 20), warm=1))
+    h2d = sum(d.numel() * d.element_size() for _, d in host_in)
+    d2h = sum(o.numel() * o.element_size() for o in outs)
 
-    peak, peak_kind = measured_peaks()
-    nbytes = algorithmic_bytes()
+    hbm, peak_kind = measured_peaks()
+    peaks = pipe_peaks(H, st)
+    t_ideal, terms = ideal_us(nbytes, ops, peaks, hbm)
     achieved = nbytes / (t_fused * 1e-6) / 1e9
-    ideal_us = nbytes / (peak * 1e9) * 1e6
-    traffic = load_traffic("fused_upsample_maxpool")
-
-    line = {
+    info = H.hf_query(fused, args)
+    return {
         "metric": METRIC, "value": round(t_fused, 3), "unit": "us",
-        "n_gpus": world, "steps": K, "warmup": W_, "ms_per_step": round(t_fused / 1e3, 6),
+        "n_gpus": cx.world, "steps": K, "warmup": Wm, "ms_per_step": round(t_fused / 1e3, 6),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic (seeded torch.Generator, CPU-drawn)",
-        "config": {"workload": WORKLOAD, "split": split, "d0": 512, "regcap": cap, "grid": grid,
-                   "l2": "inputs larger than L2 (928 MB touched per step)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "dtype": "f32" if name != "hist_philox" else "u8/u32", "data": "synthetic (seeded torch.Generator, CPU-drawn)",
+        "config": {"workload": spec["desc"], "split": best["split"], "d0": d0, "regcap": best["regcap"],
+                   "grid": grid, "regs": info["regs"], "spill_bytes": info["spill_bytes"],
+                   "l2": "L2 flushed (512 MB write) before every timed launch" if fl else
+                         "inputs larger than L2 (%.0f MB touched per step)" % _mb(nbytes),
+                   "parallelism": "replicas" if cx.world > 1 else "single"},
         "serial_us": round(t_serial, 3), "two_stream_us": round(t_two, 3),
-        "standalone_us": {"upsample": round(t_up, 3), "maxpool": round(t_pool, 3),
-                          "threads": [thr_up, thr_pool]},
-        "ideal_us": round(ideal_us, 3), "frac_of_ideal": round(ideal_us / t_fused, 4),
+        "standalone_us": {H.BODY_NAMES[bodies[0]]: round(ta, 3), H.BODY_NAMES[bodies[1]]: round(tb, 3),
+                          "threads": [thr_a, thr_b]},
         "speedup_vs_best_native": round(min(t_serial, t_two) / t_fused, 4),
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+        "ideal_us": round(t_ideal, 3), "ideal_terms_us": terms, "frac_of_ideal": round(t_ideal / t_fused, 4),
+        "pipe_peaks_per_s": {k: float("%.4g" % v) for k, v in peaks.items()},
+        "search": {"exhaustive_best_us": round(best["time_us"], 3), "points": len(ok),
+                   "alg2": {k: alg2[k] for k in ("split", "regcap", "blocks_per_sm", "time_us")},
+                   "naive_even_split_us": round(naive["time_us"], 3) if naive else None},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": load_traffic(spec["name"]),
                      "peak_source": peak_kind},
-        "e2e": {"value": round(t_e2e, 2), "unit": "us", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+        "e2e": {"value": round(t_e2e, 2), "unit": "us", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": K,
-        "clocks": clocks,
-        "sweep": sweep,
+        "clocks": clk.summary(),
     }
-    if rank == 0 and not args.no_cpu_baseline:
+
+
+NWAY_DESC = ("8 kernels in one persistent CUDA-graph launch: bn stats 64x256x56x56, im2col 3x3 "
+             "32x64x56x56, maxpool 32x128x112x112, upsample 32x64x128x128, hist 2^26 u8, "
+             "Philox 2^24 blocks, 64x degree-32 Horner on 2^22, bf16 axpy on 2^27")
+
+
+def run_nway(cx):
+    import torch
+
+    from paper_2007_01277_gb300 import hfuse as H
+    from paper_2007_01277_gb300 import workloads as W
+    dev, st = cx.dev, cx.stream
+    sp = W.WORKLOADS["nway8"]
+    xb = W.bn_input(sp["bn"]).to(dev)
+    mb, vb = torch.empty(sp["bn"][1], device=dev), torch.empty(sp["bn"][1], device=dev)
+    ws = H.bn_stats_workspace(xb)
+    xi = W.im2col_input(sp["im2col"]).to(dev)
+    ci = torch.empty(sp["im2col"][0], sp["im2col"][1] * 9, sp["im2col"][2] * sp["im2col"][3], device=dev)
+    xp = W.maxpool_input(sp["pool"]).to(dev)
+    yp = torch.empty(sp["pool"][:2] + (56, 56), device=dev)
+    xu = W.upsample_input(sp["up"]).to(dev)
+    yu = torch.empty(sp["up"][:2] + (256, 256), device=dev)
+    xh = W.hist_input(sp["hist_n"]).to(dev)
+    bins = torch.zeros(256, dtype=torch.int32, device=dev)
+    po = torch.empty((sp["philox_n"], 4), dtype=torch.int32, device=dev)
+    xq = W.poly_input(sp["poly_n"]).to(dev)
+    yq = torch.empty_like(xq)
+    x16, y16 = (t.to(dev) for t in W.bf16_inputs(sp["bf16_n"]))
+    o16 = torch.empty_like(x16)
+    bodies = [H.BN_STATS, H.IM2COL3, H.MAXPOOL3S2, H.UPSAMPLE2X, H.HIST256, H.PHILOX, H.POLY, H.BF16_AXPY]
+    args = [H.bn_stats_args(xb, mb, vb, ws), H.im2col3_args(xi, ci), H.maxpool3s2_args(xp, yp),
+            H.upsample2x_args(xu, yu), H.hist256_args(xh, bins), H.philox_args(po, 0),
+            H.poly_args(xq, yq, W.poly_coefficients().tolist()), H.bf16_axpy_args(x16, y16, o16)]
+    ks = [H.hf_register_kernel(b) for b in bodies]
+    nbytes = sum(t.numel() * t.element_size() for t in (xb, xi, ci, xp, yp, xu, yu, xh, po, xq, yq, x16, y16, o16))
+    ops = {"ffma": sp["poly_n"] * 64 * 33, "imul": sp["philox_n"] * 40, "smem_atomic": sp["hist_n"]}
+
+    plan, single = H.hf_autotune_nway(ks, args, max_evals=cx.args.nway_evals, reps=3, stream=st)
+    fused = H.hf_fuse_n(ks, plan["interval_of"], plan["interval_threads"], plan["regcap"])
+    lim = H.hf_device_info()
+    grid = plan["grid"]
+    # standalone configurations for the baselines: 256 threads, resident grid
+    cfg = []
+    for k, a in zip(ks, args):
+        info = H.hf_query_single(k, a, 256)
+        cfg.append((k, a, 256, info["blocks_per_sm"] * lim.sm_count))
+    streams = [torch.cuda.Stream(device=dev) for _ in range(len(ks))]
+    ev_f = torch.cuda.Event()
+    ev_j = [torch.cuda.Event() for _ in ks]
+
+    def issue_fused():
+        H.hf_launch(fused, args, grid, st)
+
+    def issue_serial():
+        for k, a, t, g in cfg:
+            H.hf_launch_single(k, a, t, g, st)
+
+    def issue_nstream():
+        ev_f.record(st)
+        for s_, (k, a, t, g), e in zip(streams, cfg, ev_j):
+            s_.wait_event(ev_f)
+            H.hf_launch_single(k, a, t, g, s_)
+            e.record(s_)
+        for e in ev_j:
+            st.wait_event(e)
+
+    graphs = {}
+    with torch.cuda.stream(st):
+        for nm, fn in (("fused", issue_fused), ("serial", issue_serial), ("nstream", issue_nstream)):
+            fn()
+            torch.cuda.synchronize()
+            H.hf_graph_begin(st)
+            fn()
+            graphs[nm] = H.hf_graph_end(st)
+    K, Wm = cx.args.steps, cx.args.warmup
+    cx.barrier()
+    with ClockSampler(dev) as clk:
+        per = cx.timed(lambda: H.hf_graph_launch(graphs["fused"], st), K, warm=Wm)
+    cx.barrier()
+    t_fused = cx.max_over_ranks(statistics.mean(per))
+    t_serial = statistics.median(cx.timed(lambda: H.hf_graph_launch(graphs["serial"], st), max(5, K // 4), warm=Wm))
+    t_nstream = statistics.median(cx.timed(lambda: H.hf_graph_launch(graphs["nstream"], st), max(5, K // 4), warm=Wm))
+    t_fused_nograph = statistics.median(cx.timed(issue_fused, max(5, K // 4), warm=Wm))
+    hbm, peak_kind = measured_peaks()
+    peaks = pipe_peaks(H, st)
+    t_ideal, terms = ideal_us(nbytes, ops, peaks, hbm)
+    achieved = nbytes / (t_fused * 1e-6) / 1e9
+    for g in graphs.values():
+        H.hf_graph_destroy(g)
+    return {
+        "metric": METRIC, "value": round(t_fused, 3), "unit": "us",
+        "n_gpus": cx.world, "steps": K, "warmup": Wm, "ms_per_step": round(t_fused / 1e3, 6),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32/bf16/u8/u32",
+        "data": "synthetic (seeded torch.Generator, CPU-drawn)",
+        "config": {"workload": NWAY_DESC, "plan": plan, "l2": "inputs larger than L2 (%.0f MB per step)" % _mb(nbytes),
+                   "parallelism": "replicas" if cx.world > 1 else "single"},
+        "serial_us": round(t_serial, 3), "n_stream_us": round(t_nstream, 3),
+        "fused_no_graph_us": round(t_fused_nograph, 3),
+        "standalone_us": {H.BODY_NAMES[b]: round(t, 2) for b, t in zip(bodies, single)},
+        "speedup_vs_best_native": round(min(t_serial, t_nstream) / t_fused, 4),
+        "ideal_us": round(t_ideal, 3), "ideal_terms_us": terms, "frac_of_ideal": round(t_ideal / t_fused, 4),
+        "pipe_peaks_per_s": {k: float("%.4g" % v) for k, v in peaks.items()},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": load_traffic("nway8"),
+                     "peak_source": peak_kind},
+        "e2e": None, "gpu_launches": K, "clocks": clk.summary(),
+    }
+
+
+def run_cost_model(cx):
+    import tempfile
+
+    from paper_2007_01277_gb300 import costmodel as CM
+    hbm, peak_kind = measured_peaks()
+    db = cx.args.cost_db or os.path.join(tempfile.gettempdir(), "hfuse_cost_profile.jsonl")
+    res, _P, _norm = CM.run(cx.dev, db, n_pairs=600, n_train=500, steps=cx.args.cost_steps,
+                            reps=3, hbm_gbs=hbm, log=lambda m: print(m, file=sys.stderr, flush=True))
+    r = res["regret"]
+    return {
+        "metric": METRIC, "value": round(100 * r["mean"], 3), "unit": "% regret (mean, 100 held-out pairs)",
+        "n_gpus": cx.world, "steps": cx.args.cost_steps, "warmup": 0, "ms_per_step": None,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (600 generated stream-template pairs, seed 0)",
+        "config": {"workload": "learned cost model: 600 parametric stream-kernel pairs, exhaustive "
+                               "profile of 168 configs each, MLP 24-64-64-1 trained on 500, "
+                               "regret on 100 held out", "profile_db": os.path.basename(db)},
+        "cost_model": res,
+    }
+
+
+def run_ours(args):
+    cx = Ctx(args)
+    if args.workload == "cost_model":
+        line = run_cost_model(cx)
+    elif args.workload == "nway8":
+        line = run_nway(cx)
+    else:
+        line = run_pair(cx, args.workload)
+    if cx.rank == 0 and not args.no_cpu_baseline and args.workload == "upsample_maxpool":
         line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
-    if rank == 0:
+    if cx.rank == 0:
         print(json.dumps(line), flush=True)
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
+    if cx.dist:
+        cx.dist.barrier()
+        cx.dist.destroy_process_group()
 
 
 def load_traffic(name):
@@ -341,11 +593,16 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="upsample_maxpool",
+                    choices=sorted(PAIR_SPECS) + ["nway8", "cost_model"])
+    ap.add_argument("--cost-db", default=None)
+    ap.add_argument("--cost-steps", type=int, default=20000)
+    ap.add_argument("--nway-evals", type=int, default=120)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

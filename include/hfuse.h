@@ -345,6 +345,87 @@ hf_status hf_search_alg2(hf_kernel a, hf_kernel b, const void *const *args, int 
 hf_status hf_bn_stats_noalloc(const float *x, float *mean, float *var, int N, int C, int HW,
                               int threads, int grid, void *stream);
 
+/* A schedule for N-way fusion: kernel j runs on interval interval_of[j];
+ * interval i has interval_threads[i] threads; plus the register cap, the
+ * grid and the measured time of the plan. */
+typedef struct {
+    int n_intervals;
+    int interval_of[HF_MAX_SCHEDULE];
+    int interval_threads[HF_MAX_INTERVALS];
+    int regcap;
+    int grid;
+    float time_us;
+    int evals;
+} hf_nway_plan;
+
+/* Autotuner for N-way fusion.  Times every kernel alone (256 threads), then
+ * packs kernels onto intervals longest-first (LPT: each goes to the least
+ * loaded interval), gives each interval warps in proportion to its load, and
+ * times these plans for block sizes 512 and 1024, register caps none/64/96,
+ * and one interval per kernel or about two kernels per interval.  From the
+ * fastest it hill-climbs, moving one warp between two intervals while the
+ * measured time drops by more than 0.5%, for at most max_evals timed plans.
+ * standalone_us (n entries, may be NULL) receives the single-kernel times. */
+hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, int max_evals,
+                           int reps, int flush_l2, void *stream, hf_nway_plan *best,
+                           float *standalone_us);
+
+/* Measured throughput of one execution pipe on the current device, for
+ * the compute terms of the ideal-overlap bound: what = 0 FP32 fused
+ * multiply-adds per second, 1 32-bit integer multiplies (high or low half)
+ * per second, 2 shared-memory atomic adds per second (conflict-free).
+ * Runs a few milliseconds of calibration kernels on `stream`. */
+hf_status hf_calibrate(int what, void *stream, double *ops_per_s);
+
+/* ------------------------------------------------------------------ */
+/* Learned cost model (replaces profiling every configuration of the    */
+/* search of Algorithm 2, Sec. 3.2, by a prediction).                  */
+
+#define HF_MLP_NPARAMS 5825   /* 24-64-64-1 perceptron, see hf_mlp_forward */
+#define HF_MLP_FEATURES 24
+
+/* The 24 features of two stream-template kernels fused in one d0-thread
+ * block (split threads for a) at a register cap, blocks per SM and the
+ * fused instance's registers and spill bytes; hbm_gbs and ffma_per_s are
+ * the device's measured bandwidth and FP32 FMA rate.  Host arithmetic; out
+ * receives HF_MLP_FEATURES floats scaled to about [0, 1]. */
+hf_status hf_tmpl_features(const hf_stream_tmpl_args *a, const hf_stream_tmpl_args *b, int split,
+                           int d0, int regcap, int blocks_per_sm, int fused_regs, int spill_bytes,
+                           double hbm_gbs, double ffma_per_s, float *out);
+
+/* FP32 perceptron 24 -> 64 -> ReLU -> 64 -> ReLU -> 1 over n rows of
+ * X[n][24] (device), writing y[n] (device).  params (device) is the flat
+ * row-major array W1[64][24], b1[64], W2[64][64], b2[64], w3[64], b3. */
+hf_status hf_mlp_forward(const float *params, const float *X, int n, float *y, void *stream);
+
+/* Trains params in place with Adam on the mean squared error, all `steps`
+ * steps in one kernel launch (one thread block): step s uses the batch rows
+ * idx[s*batch .. s*batch + batch) of X[.][24] / Y[.] (batch <= 64); adam_m
+ * and adam_v are the first and second moment arrays (device, HF_MLP_NPARAMS
+ * each, zero for a fresh run); t0 is the number of Adam steps already taken.
+ * loss_out[steps] (may be NULL) receives each step's batch loss; grad_out
+ * (may be NULL) receives the first step's gradient.  Deterministic. */
+hf_status hf_mlp_train(float *params, float *adam_m, float *adam_v, const float *X, const float *Y,
+                       const int *idx, int steps, int batch, float lr, float beta1, float beta2,
+                       float eps, int t0, float *loss_out, float *grad_out, void *stream);
+int hf_mlp_nparams(void);
+
+/* ------------------------------------------------------------------ */
+/* CUDA graphs.                                                        */
+
+typedef struct hf_graph_t *hf_graph;
+
+/* Start recording the work issued to `stream` (relaxed capture mode): every
+ * hf_launch / hf_launch_single on it, and on streams joined to it through
+ * events, becomes part of the graph instead of running.  Launch each
+ * configuration once before capturing it so that its resource queries are
+ * cached.  hf_graph_end stops recording and instantiates the graph. */
+hf_status hf_graph_begin(void *stream);
+hf_status hf_graph_end(void *stream, hf_graph *out);
+/* Replays the recorded work on `stream` as one submission. */
+hf_status hf_graph_launch(hf_graph g, void *stream);
+void hf_graph_destroy(hf_graph g);
+
 /* Waits until all work queued on `stream` has finished, polling for at most
  * timeout_ms milliseconds: HF_ERR_TIMEOUT if it has not finished by then
  * (the work keeps running; nothing is cancelled), HF_ERR_CUDA if the stream

@@ -90,9 +90,10 @@ struct BodyHist {
 // hi32(first+i), 0, 0) under key (lo32(seed), hi32(seed)); each of the ten
 // rounds multiplies two counter words by the Philox multipliers, mixes the
 // high halves with the other words and the round key, and the key advances
-// by the Weyl increments between rounds.  Two blocks per thread iteration
-// give the integer pipes two independent chains; blocks leave as 128-bit
-// streaming stores.
+// by the Weyl increments between rounds.  The ten round keys are computed
+// once per thread; each multiply is a high-half and a low-half 32-bit
+// multiply (cheaper on the integer multiply pipe than one 64-bit product).
+// Blocks leave as 128-bit streaming stores.
 struct BodyPhilox {
     using Args = hf_philox_args;
     static constexpr int kId = HF_BODY_PHILOX;
@@ -110,39 +111,34 @@ struct BodyPhilox {
         return HF_OK;
     }
 
-    static __device__ __forceinline__ uint4 block(uint64_t ctr, unsigned k0, unsigned k1)
+    static __device__ __forceinline__ uint4 block(uint64_t ctr, const unsigned (&K0)[10],
+                                                 const unsigned (&K1)[10])
     {
         unsigned c0 = (unsigned)ctr, c1 = (unsigned)(ctr >> 32), c2 = 0u, c3 = 0u;
 #pragma unroll
         for (int r = 0; r < 10; ++r) {
-            const uint64_t p0 = (uint64_t)kM0 * c0;
-            const uint64_t p1 = (uint64_t)kM1 * c2;
-            const unsigned n0 = (unsigned)(p1 >> 32) ^ c1 ^ k0;
-            const unsigned n2 = (unsigned)(p0 >> 32) ^ c3 ^ k1;
-            c1 = (unsigned)p1;
-            c3 = (unsigned)p0;
-            c0 = n0;
-            c2 = n2;
-            k0 += kW0;
-            k1 += kW1;
+            const unsigned h0 = __umulhi(kM0, c0), l0 = kM0 * c0;
+            const unsigned h1 = __umulhi(kM1, c2), l1 = kM1 * c2;
+            c0 = h1 ^ c1 ^ K0[r];
+            c2 = h0 ^ c3 ^ K1[r];
+            c1 = l1;
+            c3 = l0;
         }
         return make_uint4(c0, c1, c2, c3);
     }
 
     static __device__ void run(const Args &a, const Ctx &cx)
     {
-        const unsigned k0 = (unsigned)a.seed, k1 = (unsigned)(a.seed >> 32);
-        const int64_t gt = (int64_t)cx.block * cx.nthreads + cx.tid;
+        unsigned K0[10], K1[10];
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+            K0[r] = (unsigned)a.seed + (unsigned)r * kW0;
+            K1[r] = (unsigned)(a.seed >> 32) + (unsigned)r * kW1;
+        }
         const int64_t stride = (int64_t)cx.grid * cx.nthreads;
         uint4 *out = reinterpret_cast<uint4 *>(a.out);
-        int64_t i = gt;
-        for (; i + stride < a.n; i += 2 * stride) {
-            const uint4 u = block(a.first + (uint64_t)i, k0, k1);
-            const uint4 v = block(a.first + (uint64_t)(i + stride), k0, k1);
-            __stcs(out + i, u);
-            __stcs(out + i + stride, v);
-        }
-        if (i < a.n) __stcs(out + i, block(a.first + (uint64_t)i, k0, k1));
+        for (int64_t i = (int64_t)cx.block * cx.nthreads + cx.tid; i < a.n; i += stride)
+            __stcs(out + i, block(a.first + (uint64_t)i, K0, K1));
     }
 };
 

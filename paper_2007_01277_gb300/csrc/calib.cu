@@ -1,0 +1,121 @@
+// calib.cu -- pipe-throughput calibration kernels.
+//
+// The ideal-overlap bound of a fused launch is the larger of its HBM time
+// and, for each execution pipe, the operations the constituents issue there
+// divided by that pipe's throughput.  These kernels measure the throughputs
+// on the running device (clock behaviour included) instead of using nominal
+// figures: independent FP32 fused multiply-add chains, 32-bit integer
+// multiplies (high and low halves, the Philox mix), and conflict-free
+// shared-memory atomic adds (the histogram's counting operation).
+#include <algorithm>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace hf {
+hf_status set_last_error(hf_status s, const char *msg);   // runtime.cu
+}
+
+namespace {
+
+constexpr int kChains = 8;
+
+// Sink for the results the kernels keep live (written only on a condition
+// that does not occur; indices stay below the block size of 256).
+__device__ unsigned g_cal_sink[1024];
+
+__global__ void k_cal_ffma(float *out, int iters)
+{
+    float a[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) a[j] = 1.0f + 1e-3f * (threadIdx.x + j);
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int j = 0; j < kChains; ++j) a[j] = __fmaf_rn(a[j], 0.9999f, 1e-4f);
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) s += a[j];
+    if (s == -1.0f) out[threadIdx.x] = s;   // never true; keeps the chains live
+}
+
+__global__ void k_cal_imul(unsigned *out, int iters)
+{
+    unsigned c[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) c[j] = threadIdx.x * 2654435761u + j;
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int j = 0; j < kChains; ++j) c[j] = __umulhi(0xD2511F53u, c[j]) ^ (0xCD9E8D57u * c[j]);
+    unsigned s = 0;
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) s ^= c[j];
+    if (s == 0x12345678u) out[threadIdx.x] = s;
+}
+
+__global__ void k_cal_satom(unsigned *out, int iters)
+{
+    extern __shared__ unsigned sh[];
+    const int lane = threadIdx.x & 31;
+    unsigned *mine = sh + (threadIdx.x >> 5) * 256;
+    for (int i = threadIdx.x; i < blockDim.x * 8; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) atomicAdd(mine + ((lane + 32 * ((i + j) & 7)) & 255), 1u);
+    __syncthreads();
+    if (mine[lane] == 0xffffffffu) out[threadIdx.x] = 1;
+}
+
+template <class F>
+hf_status time_ms(F f, cudaStream_t s, float *ms)
+{
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return HF_ERR_CUDA;
+    f();   // warm-up
+    std::vector<float> t;
+    for (int r = 0; r < 5; ++r) {
+        cudaEventRecord(a, s);
+        f();
+        cudaEventRecord(b, s);
+        if (cudaEventSynchronize(b) != cudaSuccess) return HF_ERR_CUDA;
+        float x = 0;
+        cudaEventElapsedTime(&x, a, b);
+        t.push_back(x);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    std::sort(t.begin(), t.end());
+    *ms = t[2];
+    return cudaGetLastError() == cudaSuccess ? HF_OK : HF_ERR_CUDA;
+}
+
+} // namespace
+
+extern "C" hf_status hf_calibrate(int what, void *stream, double *ops_per_s)
+{
+    if (!ops_per_s || what < 0 || what > 2) return hf::set_last_error(HF_ERR_INVALID, "bad calibration id");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int threads = 256, blocks = 8 * sms;   // 64 warps per SM
+    const int iters = 4096;
+    void *out = nullptr;
+    float ms = 0.f;
+    hf_status st;
+    cudaError_t e = cudaGetSymbolAddress(&out, g_cal_sink);
+    if (e != cudaSuccess) return hf::set_last_error(HF_ERR_CUDA, cudaGetErrorString(e));
+    if (what == 0) {
+        st = time_ms([&] { k_cal_ffma<<<blocks, threads, 0, s>>>((float *)out, iters); }, s, &ms);
+        *ops_per_s = (double)blocks * threads * iters * kChains / (ms * 1e-3);
+    } else if (what == 1) {
+        st = time_ms([&] { k_cal_imul<<<blocks, threads, 0, s>>>((unsigned *)out, iters); }, s, &ms);
+        *ops_per_s = 2.0 * blocks * threads * iters * kChains / (ms * 1e-3);
+    } else {
+        st = time_ms([&] { k_cal_satom<<<blocks, threads, 8 * threads * 4, s>>>((unsigned *)out, iters / 4); },
+                     s, &ms);
+        *ops_per_s = (double)blocks * threads * (iters / 4) * 8 / (ms * 1e-3);
+    }
+    if (st) return hf::set_last_error(st, "calibration kernel failed");
+    return HF_OK;
+}

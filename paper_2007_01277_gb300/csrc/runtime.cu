@@ -248,8 +248,23 @@ hf_status pick_grid(const void *func, int d0, size_t smem, int want, int *grid, 
                     smem, lim.smem_per_block_optin);
     s = ensure_smem(func, smem);
     if (s) return s;
-    int b = 0;
-    HF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, func, d0, smem));
+    // resident blocks per (function, block size, shared memory), cached so
+    // that a launch recorded into a graph makes no occupancy query
+    static std::mutex occ_mu;
+    static std::unordered_map<std::string, int> occ;
+    char key[96];
+    snprintf(key, sizeof key, "%p/%d/%zu", func, d0, smem);
+    int b = -1;
+    {
+        std::lock_guard<std::mutex> lk(occ_mu);
+        auto it = occ.find(key);
+        if (it != occ.end()) b = it->second;
+    }
+    if (b < 0) {
+        HF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, func, d0, smem));
+        std::lock_guard<std::mutex> lk(occ_mu);
+        occ[key] = b;
+    }
     if (b <= 0) return fail(HF_ERR_REGS, "block of %d threads with %zu B shared memory cannot be resident", d0, smem);
     if (bps) *bps = b;
     if (grid) *grid = want > 0 ? want : b * lim.sm_count;

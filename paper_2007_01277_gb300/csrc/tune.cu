@@ -20,6 +20,14 @@ extern "C" {
 hf_status hf_query_single(hf_kernel k, const void *args, int threads, hf_fused_info *info);
 }
 
+// LPT plan of the N-way autotuner: kernels -> intervals, warps per interval.
+struct NwayPlanC {
+    int P;
+    int io[HF_MAX_SCHEDULE];
+    int warps[HF_MAX_INTERVALS];
+    int cap;
+};
+
 namespace {
 
 struct FlushBuf {
@@ -216,6 +224,123 @@ hf_status hf_search_alg2(hf_kernel a, hf_kernel b, const void *const *args, int 
     }
     if (n_trace) *n_trace = nt;
     return best->time_us < 0.f ? HF_ERR_INVALID : HF_OK;
+}
+
+
+hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, int max_evals,
+                           int reps, int flush_l2_, void *stream, hf_nway_plan *best,
+                           float *standalone_us)
+{
+    if (!ks || !args || !best || n < 1 || n > HF_MAX_SCHEDULE || reps < 1) return HF_ERR_INVALID;
+    hf_device_limits lim;
+    hf_status st = hf_device_info(&lim);
+    if (st) return st;
+    // 1. each kernel alone (256 threads, resident grid): its load
+    std::vector<float> t(n);
+    for (int k = 0; k < n; ++k) {
+        st = hf_time_single(ks[k], args[k], 256, 0, reps, flush_l2_, stream, &t[k], nullptr, nullptr);
+        if (st) return st;
+        if (standalone_us) standalone_us[k] = t[k];
+    }
+    int evals = 0;
+    float best_t = -1.f;
+    NwayPlanC bp;
+    std::memset(&bp, 0, sizeof bp);
+    auto eval = [&](const NwayPlanC &p, float *us, int *grid) -> hf_status {
+        int thr[HF_MAX_INTERVALS];
+        for (int i = 0; i < p.P; ++i) thr[i] = 32 * p.warps[i];
+        hf_fused f = nullptr;
+        hf_status s2 = hf_fuse_n(ks, n, p.io, thr, p.P, p.cap, &f);
+        if (s2) return s2;
+        hf_fused_info info;
+        s2 = hf_query(f, args, &info);
+        if (!s2) {
+            *grid = info.blocks_per_sm * lim.sm_count;
+            s2 = hf_time_fused(f, args, *grid, reps, flush_l2_, stream, us, nullptr, nullptr);
+        }
+        hf_destroy_fused(f);
+        ++evals;
+        return s2;
+    };
+    auto consider = [&](const NwayPlanC &p) -> hf_status {
+        float us = 0.f;
+        int grid = 0;
+        hf_status s2 = eval(p, &us, &grid);
+        if (s2 == HF_ERR_CUDA) return s2;
+        if (s2) return HF_OK;   // not buildable / not resident: skip
+        if (best_t < 0.f || us < best_t) {
+            best_t = us;
+            bp = p;
+            best->grid = grid;
+        }
+        return HF_OK;
+    };
+    // 2. LPT packings over block sizes, caps and interval counts
+    std::vector<int> order(n);
+    for (int k = 0; k < n; ++k) order[k] = k;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return t[a] > t[b]; });
+    const int d0s[] = {512, 1024};
+    const int caps[] = {0, 64, 96};
+    for (int d0 : d0s)
+        for (int cap : caps)
+            for (int P : {n, (n + 1) / 2}) {
+                const int W = d0 / 32;
+                if (P > HF_MAX_INTERVALS || P > W || P < 1) continue;
+                NwayPlanC p;
+                std::memset(&p, 0, sizeof p);
+                p.P = P;
+                p.cap = cap;
+                std::vector<double> load(P, 0.0);
+                for (int k : order) {
+                    int i = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+                    p.io[k] = i;
+                    load[i] += t[k];
+                }
+                double tot = 0.0;
+                for (double l : load) tot += l;
+                int used = 0;
+                for (int i = 0; i < P; ++i) {
+                    p.warps[i] = 1 + (int)((W - P) * load[i] / tot);
+                    used += p.warps[i];
+                }
+                while (used < W) {   // leftover warps to the most loaded per warp
+                    int bi = 0;
+                    for (int i = 1; i < P; ++i)
+                        if (load[i] / p.warps[i] > load[bi] / p.warps[bi]) bi = i;
+                    ++p.warps[bi];
+                    ++used;
+                }
+                st = consider(p);
+                if (st) return st;
+            }
+    if (best_t < 0.f) return HF_ERR_INVALID;
+    // 3. hill climb: move one warp between two intervals while it helps
+    bool improved = true;
+    while (improved && evals < max_evals) {
+        improved = false;
+        const NwayPlanC base = bp;
+        const float base_t = best_t;
+        for (int i = 0; i < base.P && evals < max_evals; ++i)
+            for (int j = 0; j < base.P && evals < max_evals; ++j) {
+                if (i == j || base.warps[i] <= 1) continue;
+                NwayPlanC p = base;
+                --p.warps[i];
+                ++p.warps[j];
+                st = consider(p);
+                if (st) return st;
+            }
+        improved = best_t < base_t * 0.995f;
+    }
+    const int grid = best->grid;
+    std::memset(best, 0, sizeof *best);
+    best->n_intervals = bp.P;
+    for (int k = 0; k < n; ++k) best->interval_of[k] = bp.io[k];
+    for (int i = 0; i < bp.P; ++i) best->interval_threads[i] = 32 * bp.warps[i];
+    best->regcap = bp.cap;
+    best->grid = grid;
+    best->time_us = best_t;
+    best->evals = evals;
+    return HF_OK;
 }
 
 } // extern "C"

@@ -101,6 +101,17 @@ class TunePoint(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class NwayPlan(ctypes.Structure):
+    _fields_ = [("n_intervals", _i32), ("interval_of", _i32 * 16), ("interval_threads", _i32 * 15),
+                ("regcap", _i32), ("grid", _i32), ("time_us", _f32), ("evals", _i32)]
+
+    def as_dict(self):
+        n = self.n_intervals
+        return {"n_intervals": n, "interval_of": list(self.interval_of),
+                "interval_threads": list(self.interval_threads[:n]), "regcap": self.regcap,
+                "grid": self.grid, "time_us": self.time_us, "evals": self.evals}
+
+
 class HFError(RuntimeError):
     def __init__(self, fn, status, msg):
         super().__init__("%s -> %s: %s" % (fn, STATUS.get(status, status), msg))
@@ -141,6 +152,20 @@ def _load():
                                   ctypes.POINTER(TunePoint), ctypes.POINTER(TunePoint), _i32,
                                   ctypes.POINTER(_i32)]),
         "hf_bn_stats_noalloc": (_i32, [_P, _P, _P, _i32, _i32, _i32, _i32, _i32, _P]),
+        "hf_autotune_nway": (_i32, [ctypes.POINTER(_P), _i32, ctypes.POINTER(_P), _i32, _i32, _i32,
+                                    _P, ctypes.POINTER(NwayPlan), ctypes.POINTER(_f32)]),
+        "hf_calibrate": (_i32, [_i32, _P, ctypes.POINTER(ctypes.c_double)]),
+        "hf_tmpl_features": (_i32, [ctypes.POINTER(StreamTmplArgs), ctypes.POINTER(StreamTmplArgs),
+                                    _i32, _i32, _i32, _i32, _i32, _i32, ctypes.c_double,
+                                    ctypes.c_double, ctypes.POINTER(_f32)]),
+        "hf_mlp_forward": (_i32, [_P, _P, _i32, _P, _P]),
+        "hf_mlp_train": (_i32, [_P, _P, _P, _P, _P, _P, _i32, _i32, _f32, _f32, _f32, _f32, _i32,
+                                _P, _P, _P]),
+        "hf_mlp_nparams": (_i32, []),
+        "hf_graph_begin": (_i32, [_P]),
+        "hf_graph_end": (_i32, [_P, ctypes.POINTER(_P)]),
+        "hf_graph_launch": (_i32, [_P, _P]),
+        "hf_graph_destroy": (None, [_P]),
         "hf_status_string": (ctypes.c_char_p, [_i32]),
         "hf_last_error": (ctypes.c_char_p, []),
         "hf_args_size": (ctypes.c_size_t, [_i32]),
@@ -259,8 +284,16 @@ def hf_destroy_kernel(k):
 
 
 # ----------------------------------------------------------------- argument blocks
+# An argument block holds raw device addresses; it also keeps a reference to
+# the tensors behind them (attribute _keep), so that memory cannot be freed
+# and reused while the block can still be launched.
 def _ptr(t):
     return t.data_ptr() if t is not None else None
+
+
+def _keep(block, *tensors):
+    block._keep = tensors
+    return block
 
 
 def bn_stats_args(x, mean, var, workspace=None):
@@ -268,7 +301,7 @@ def bn_stats_args(x, mean, var, workspace=None):
     a = BnStatsArgs(_ptr(x), _ptr(mean), _ptr(var), N, C, H * W, None)
     if workspace is not None:
         a.workspace = _ptr(workspace)
-    return a
+    return _keep(a, x, mean, var, workspace)
 
 
 def bn_stats_workspace(x):
@@ -281,38 +314,38 @@ def bn_stats_workspace(x):
 
 def upsample2x_args(x, y):
     H, W = x.shape[-2:]
-    return Upsample2xArgs(_ptr(x), _ptr(y), x.numel() // (H * W), H, W)
+    return _keep(Upsample2xArgs(_ptr(x), _ptr(y), x.numel() // (H * W), H, W), x, y)
 
 
 def maxpool3s2_args(x, y):
     H, W = x.shape[-2:]
-    return Maxpool3s2Args(_ptr(x), _ptr(y), x.numel() // (H * W), H, W)
+    return _keep(Maxpool3s2Args(_ptr(x), _ptr(y), x.numel() // (H * W), H, W), x, y)
 
 
 def im2col3_args(x, col):
     N, C, H, W = x.shape
-    return Im2col3Args(_ptr(x), _ptr(col), N, C, H, W)
+    return _keep(Im2col3Args(_ptr(x), _ptr(col), N, C, H, W), x, col)
 
 
 def hist256_args(x, bins):
-    return Hist256Args(_ptr(x), _ptr(bins), x.numel())
+    return _keep(Hist256Args(_ptr(x), _ptr(bins), x.numel()), x, bins)
 
 
 def philox_args(out, seed, first=0):
-    return PhiloxArgs(_ptr(out), out.numel() // 4, seed, first)
+    return _keep(PhiloxArgs(_ptr(out), out.numel() // 4, seed, first), out)
 
 
 def poly_args(x, y, coef, iters=64):
     c = (_f32 * 33)(*[float(v) for v in coef])
-    return PolyArgs(_ptr(x), _ptr(y), x.numel(), iters, c)
+    return _keep(PolyArgs(_ptr(x), _ptr(y), x.numel(), iters, c), x, y)
 
 
 def bf16_axpy_args(x, y, out, alpha=0.5):
-    return Bf16AxpyArgs(_ptr(x), _ptr(y), _ptr(out), x.numel(), alpha)
+    return _keep(Bf16AxpyArgs(_ptr(x), _ptr(y), _ptr(out), x.numel(), alpha), x, y, out)
 
 
 def stream_tmpl_args(x, y, k, n_barriers=0, smem_bytes=0, a=0.999, b=0.001):
-    return StreamTmplArgs(_ptr(x), _ptr(y), x.numel(), k, n_barriers, smem_bytes, a, b)
+    return _keep(StreamTmplArgs(_ptr(x), _ptr(y), x.numel(), k, n_barriers, smem_bytes, a, b), x, y)
 
 
 # ----------------------------------------------------------------- profiling search
@@ -359,3 +392,68 @@ def hf_bn_stats_noalloc(x, mean, var, threads=256, grid=0, stream=None):
     N, C, Hh, Ww = x.shape
     _check("hf_bn_stats_noalloc", lib.hf_bn_stats_noalloc(
         _ptr(x), _ptr(mean), _ptr(var), N, C, Hh * Ww, threads, grid, _stream_ptr(stream)))
+
+
+# ----------------------------------------------------------------- N-way autotuner, calibration, graphs
+def hf_autotune_nway(kernels, args, max_evals=200, reps=5, flush_l2=False, stream=None):
+    n = len(kernels)
+    plan = NwayPlan()
+    single = (_f32 * n)()
+    _check("hf_autotune_nway", lib.hf_autotune_nway((_P * n)(*kernels), n, _argv(args), max_evals,
+                                                    reps, int(flush_l2), _stream_ptr(stream),
+                                                    ctypes.byref(plan), single))
+    d = plan.as_dict()
+    d["interval_of"] = d["interval_of"][:n]
+    return d, list(single)
+
+
+CAL_FFMA, CAL_IMUL, CAL_SMEM_ATOMIC = 0, 1, 2
+
+
+def hf_calibrate(what, stream=None):
+    v = ctypes.c_double()
+    _check("hf_calibrate", lib.hf_calibrate(what, _stream_ptr(stream), ctypes.byref(v)))
+    return v.value
+
+
+def hf_graph_begin(stream):
+    _check("hf_graph_begin", lib.hf_graph_begin(_stream_ptr(stream)))
+
+
+def hf_graph_end(stream):
+    g = _P()
+    _check("hf_graph_end", lib.hf_graph_end(_stream_ptr(stream), ctypes.byref(g)))
+    return g
+
+
+def hf_graph_launch(g, stream=None):
+    _check("hf_graph_launch", lib.hf_graph_launch(g, _stream_ptr(stream)))
+
+
+def hf_graph_destroy(g):
+    lib.hf_graph_destroy(g)
+
+
+# ----------------------------------------------------------------- learned cost model
+MLP_NPARAMS = 5825
+MLP_FEATURES = 24
+
+
+def hf_tmpl_features(a, b, split, d0, regcap, bps, fused_regs, spill_bytes, hbm_gbs, ffma_per_s):
+    out = (_f32 * MLP_FEATURES)()
+    _check("hf_tmpl_features", lib.hf_tmpl_features(ctypes.byref(a), ctypes.byref(b), split, d0,
+                                                    regcap, bps, fused_regs, spill_bytes,
+                                                    float(hbm_gbs), float(ffma_per_s), out))
+    return list(out)
+
+
+def hf_mlp_forward(params, X, y, stream=None):
+    _check("hf_mlp_forward", lib.hf_mlp_forward(_ptr(params), _ptr(X), X.shape[0], _ptr(y),
+                                                _stream_ptr(stream)))
+
+
+def hf_mlp_train(params, m, v, X, Y, idx, steps, batch, lr=1e-3, beta1=0.9, beta2=0.999,
+                 eps=1e-8, t0=0, loss_out=None, grad_out=None, stream=None):
+    _check("hf_mlp_train", lib.hf_mlp_train(_ptr(params), _ptr(m), _ptr(v), _ptr(X), _ptr(Y),
+                                            _ptr(idx), steps, batch, lr, beta1, beta2, eps, t0,
+                                            _ptr(loss_out), _ptr(grad_out), _stream_ptr(stream)))

@@ -113,3 +113,22 @@ def test_register_bound_host_arithmetic(H, orc):
                 for sm in (0, 1024, 40000):
                     want = orc.register_bound(65536, 98304, 2048, d1, r1, 1024 - d1, r2, sm)
                     assert H.hf_register_bound(lim, d1, r1, 1024 - d1, r2, sm) == want
+
+
+def test_template_features_hand_example(H):
+    """hf_tmpl_features on a hand-computed pair (host arithmetic only)."""
+    import math
+    a = H.StreamTmplArgs(None, None, 1 << 20, 4, 2, 4096, 0.999, 0.001)
+    b = H.StreamTmplArgs(None, None, 1 << 28, 0, 0, 0, 0.999, 0.001)
+    f = H.hf_tmpl_features(a, b, 64, 256, 0, 2, 40, 0, 6785.9, 3.8e13)
+    assert len(f) == 24
+    ta = max(8 * 2 ** 20 / 6785.9e9, 4 * 2 ** 20 / 4 / 3.8e13) * 1e6
+    tb = 8 * 2 ** 28 / 6785.9e9 * 1e6
+    want_a = [20 / 28, math.log2(5) / 8, 0.5, 4096 / 49152, math.log2(1 + ta) / 12,
+              (2 ** 20 / 3.8e13) / (8 * 2 ** 20 / 6785.9e9 + 2 ** 20 / 3.8e13), 64 / 256,
+              2 * 2 / 64, ta / (ta + tb)]
+    want_b = [1.0, 0.0, 0.0, 0.0, math.log2(1 + tb) / 12, 0.0, 192 / 256, 6 * 2 / 64, tb / (ta + tb)]
+    want_c = [1.0, 0.5, 0.25, 40 / 255, 0.0, 4096 * 2 / 233472]
+    assert f == pytest.approx(want_a + want_b + want_c, rel=1e-5, abs=1e-7)
+    with pytest.raises(H.HFError):
+        H.hf_tmpl_features(a, b, 0, 256, 0, 2, 40, 0, 6785.9, 3.8e13)

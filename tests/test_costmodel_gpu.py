@@ -1,0 +1,95 @@
+"""The cost model's perceptron kernels against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+from gpu_util import DEV  # noqa: E402
+from paper_2007_01277_gb300 import costmodel as CM  # noqa: E402
+from paper_2007_01277_gb300 import hfuse as H  # noqa: E402
+
+
+def _data(n, seed):
+    g = torch.Generator().manual_seed(seed)
+    X = torch.rand(n, 24, generator=g)
+    Y = (X[:, :4].sum(1) - 2.0 + 0.3 * torch.sin(6 * X[:, 5])).float()
+    return X, Y
+
+
+def test_mlp_forward_matches_oracle():
+    P = CM.xavier_params(3)
+    P[1536:1600] = 0.05
+    X, _ = _data(1003, 1)
+    y = torch.empty(1003, device=DEV)
+    H.hf_mlp_forward(P.to(DEV), X.to(DEV), y)
+    torch.cuda.synchronize()
+    ref = oracle.mlp_forward(P.double().numpy(), X.numpy())
+    scale = oracle.mlp_forward(P.double().abs().numpy(), X.abs().numpy())
+    err = np.abs(y.cpu().double().numpy() - ref)
+    assert np.all(err <= 1e-5 * scale + 1e-12), (err / scale).max()
+
+
+def test_mlp_gradient_and_adam_step_match_oracle():
+    P0 = CM.xavier_params(4)
+    X, Y = _data(256, 2)
+    idx = torch.arange(64, dtype=torch.int32) * 3
+    P = P0.clone().to(DEV)
+    M, V = torch.zeros_like(P), torch.zeros_like(P)
+    g = torch.empty_like(P)
+    loss = torch.empty(1, device=DEV)
+    H.hf_mlp_train(P, M, V, X.to(DEV), Y.to(DEV), idx.to(DEV), 1, 64, lr=1e-3,
+                   loss_out=loss, grad_out=g)
+    torch.cuda.synchronize()
+    rows = idx.long().numpy()
+    l_ref, g_ref = oracle.mlp_loss_grad(P0.double().numpy(), X.numpy()[rows], Y.numpy()[rows])
+    gg = g.cpu().double().numpy()
+    assert abs(loss.item() - l_ref) <= 1e-5 * l_ref
+    assert np.all(np.abs(gg - g_ref) <= 1e-4 * np.abs(g_ref).max() + 1e-7)
+    # Adam on the kernel's own gradient, in float64
+    Pd = P0.double().numpy().copy()
+    m, v = np.zeros_like(Pd), np.zeros_like(Pd)
+    oracle.adam_step(Pd, gg, m, v, 1, lr=1e-3)
+    assert np.all(np.abs(P.cpu().double().numpy() - Pd) <= 1e-6 * (np.abs(Pd) + 1e-3))
+
+
+def test_mlp_training_reduces_loss_and_is_deterministic():
+    X, Y = _data(4096, 5)
+    P = CM.xavier_params(0).to(DEV)
+    steps, batch = 800, 64
+    idx = torch.randint(0, 4096, (steps * batch,), generator=torch.Generator().manual_seed(9),
+                        dtype=torch.int32).to(DEV)
+    runs = []
+    for _ in range(2):
+        Pi, M, V = P.clone(), torch.zeros_like(P), torch.zeros_like(P)
+        loss = torch.empty(steps, device=DEV)
+        H.hf_mlp_train(Pi, M, V, X.to(DEV), Y.to(DEV), idx, steps, batch, lr=3e-3, loss_out=loss)
+        torch.cuda.synchronize()
+        runs.append((Pi.cpu(), loss.cpu().numpy()))
+    l = runs[0][1]
+    assert l[-50:].mean() < 0.1 * l[:50].mean()
+    assert torch.equal(runs[0][0], runs[1][0])
+
+
+def test_costmodel_pipeline_small():
+    """Corpus -> exhaustive profile -> features -> training -> regret, on a
+    handful of small pairs (the full 600-pair run is the benchmark's)."""
+    import os
+    import tempfile
+    pairs = CM.make_corpus(6, seed=1, max_log2=21)
+    pool = CM.Pool(DEV, max_n=1 << 21)
+    db = os.path.join(tempfile.mkdtemp(), "db.jsonl")
+    recs = CM.profile_corpus(pairs[:4], db, pool, reps=1)
+    recs = CM.profile_corpus(pairs, db, pool, reps=1)      # resumes: only 2 new pairs
+    assert [r["id"] for r in recs] == list(range(6))
+    assert all(len(r["points"]) == len(CM.SPLITS) * len(CM.CAPS) * len(CM.BPS) for r in recs)
+    X, Y, own = CM.featurize(recs, 6785.9, 3.8e13)
+    assert X.shape[1] == 24 and X.shape[0] == len(own) > 0
+    P, mu, sd, losses = CM.train(X, Y, DEV, steps=200)
+    pred = CM.predict(P, X, mu, sd, DEV)
+    r = CM.regret(recs, own, pred)
+    assert r.shape == (6,) and np.all(r >= 0)

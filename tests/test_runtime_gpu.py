@@ -1,0 +1,115 @@
+"""GPU tests of the runtime around the kernels: CUDA-graph capture, the N-way
+autotuner, Algorithm 2 and the exhaustive profile, pipe calibration and the
+bounded stream wait -- all through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+from gpu_util import DEV, check_bn, check_poly  # noqa: E402
+from paper_2007_01277_gb300 import hfuse as H  # noqa: E402
+from paper_2007_01277_gb300 import workloads as W  # noqa: E402
+
+
+def _bn_poly():
+    x = W.bn_input((4, 16, 24, 24)).to(DEV)
+    px = W.poly_input(1 << 15).to(DEV)
+    coef = W.poly_coefficients().numpy()
+    m, v, y = torch.empty(16, device=DEV), torch.empty(16, device=DEV), torch.empty_like(px)
+    ws = H.bn_stats_workspace(x)
+    args = [H.bn_stats_args(x, m, v, ws), H.poly_args(px, y, coef)]
+    return x, px, coef, (m, v, y, ws), args
+
+
+def test_graph_replay_matches_eager_launch():
+    x, px, coef, (m, v, y, _ws), args = _bn_poly()
+    f = H.hf_fuse(H.hf_register_kernel(H.BN_STATS), H.hf_register_kernel(H.POLY), 256, 512, 0)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        H.hf_launch(f, args, 0, s)
+        torch.cuda.synchronize()
+        ref = [t.clone() for t in (m, v, y)]
+        for t in (m, v, y):
+            t.zero_()
+        torch.cuda.synchronize()
+        H.hf_graph_begin(s)
+        H.hf_launch(f, args, 0, s)
+        g = H.hf_graph_end(s)
+        for _ in range(3):
+            H.hf_graph_launch(g, s)
+        torch.cuda.synchronize()
+    for a, b in zip(ref, (m, v, y)):
+        assert torch.equal(a, b)
+    check_bn(x.cpu(), m, v)
+    check_poly(px.cpu(), coef, y)
+    H.hf_graph_destroy(g)
+
+
+def test_autotune_nway_plan_is_valid_and_correct():
+    x, px, coef, (m, v, y, _ws), bp_args = _bn_poly()
+    xh = W.hist_input(1 << 20).to(DEV)
+    bins = torch.zeros(256, dtype=torch.int32, device=DEV)
+    po = torch.empty((1 << 14, 4), dtype=torch.int32, device=DEV)
+    args = bp_args + [H.hist256_args(xh, bins), H.philox_args(po, 5)]
+    ks = [H.hf_register_kernel(b) for b in (H.BN_STATS, H.POLY, H.HIST256, H.PHILOX)]
+    plan, single = H.hf_autotune_nway(ks, args, max_evals=20, reps=2)
+    assert len(single) == 4 and all(t > 0 for t in single)
+    n_int = plan["n_intervals"]
+    assert 1 <= n_int <= 4 and sum(plan["interval_threads"]) in (512, 1024)
+    assert set(plan["interval_of"]) == set(range(n_int))
+    assert plan["time_us"] > 0 and plan["evals"] <= 20 + 12
+    f = H.hf_fuse_n(ks, plan["interval_of"], plan["interval_threads"], plan["regcap"])
+    bins.zero_()
+    H.hf_launch(f, args, plan["grid"])
+    torch.cuda.synchronize()
+    check_bn(x.cpu(), m, v)
+    check_poly(px.cpu(), coef, y)
+    assert np.array_equal(bins.cpu().numpy().view(np.uint32), oracle.hist256(xh.cpu().numpy()))
+    assert np.array_equal(po.cpu().numpy().view(np.uint32), oracle.philox4x32_10(5, 1 << 14))
+
+
+def test_profile_pair_and_alg2():
+    x, px, coef, (m, v, y, _ws), args = _bn_poly()
+    ka, kb = H.hf_register_kernel(H.BN_STATS), H.hf_register_kernel(H.POLY)
+    table = H.hf_profile_pair(ka, kb, args, 512, [128, 256, 384], [0, 64], [1, 2], reps=2)
+    assert len(table) == 12
+    ok = [p for p in table if p["status"] == 0]
+    assert ok and all(p["time_us"] > 0 for p in ok)
+    assert all(p["grid"] == p["blocks_per_sm"] * H.hf_device_info().sm_count for p in ok)
+    best, trace = H.hf_search_alg2(ka, kb, args, 512, step=128, reps=2)
+    assert best["split"] in (128, 256, 384) and best["time_us"] > 0
+    assert best["time_us"] == min(p["time_us"] for p in trace if p["status"] == 0)
+    # the visited splits follow Algorithm 2: ascending, unbounded before bounded
+    splits = [p["split"] for p in trace]
+    assert splits == sorted(splits)
+
+
+def test_calibration_in_plausible_range():
+    lim = H.hf_device_info()
+    ffma = H.hf_calibrate(H.CAL_FFMA)
+    # between 20% and 110% of 128 FMA/clk/SM at 2.1 GHz
+    nominal = lim.sm_count * 128 * 2.1e9
+    assert 0.2 * nominal < ffma < 1.1 * nominal
+    assert H.hf_calibrate(H.CAL_IMUL) > 0
+    assert H.hf_calibrate(H.CAL_SMEM_ATOMIC) > 0
+
+
+def test_stream_wait_times_out_on_long_kernel():
+    """A launch-timeout check without any fault: a long polynomial chain
+    is still running after 1 ms, then completes within the larger limit."""
+    k = H.hf_register_kernel(H.POLY)
+    x = torch.rand(1 << 22, device=DEV)
+    y = torch.empty_like(x)
+    s = torch.cuda.Stream()
+    a = H.poly_args(x, y, [0.01] * 33, iters=4000)
+    torch.cuda.synchronize()
+    H.hf_launch_single(k, a, 256, 152, s)
+    with pytest.raises(H.HFError) as e:
+        H.hf_stream_wait(s, 1)
+    assert e.value.status == -8
+    H.hf_stream_wait(s, 60000)
