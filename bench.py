@@ -517,12 +517,13 @@ def run_ours(args):
 def load_traffic(name):
     """DRAM bytes per launch of the fused kernel from the committed ncu
     summary (dram__bytes_read.sum + dram__bytes_write.sum), if any."""
-    p = os.path.join(ROOT, "profiles", name + ".json")
-    if os.path.exists(p):
-        try:
-            return json.load(open(p)).get("traffic_bytes_per_launch")
-        except (OSError, ValueError):
-            return None
+    p = os.path.join(ROOT, "profiles", name + "_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        parts = line.split()
+        if len(parts) == 2 and parts[0] == "traffic_bytes_per_launch":
+            return int(parts[1])
     return None
 
 
