@@ -213,6 +213,14 @@ void hf_destroy_fused(hf_fused f);
  * the grid, so any grid >= 1 computes the full result. */
 hf_status hf_launch(hf_fused f, const void *const *args, int grid, void *stream);
 
+/* hf_launch of an N-way fused kernel that also records, per interval i,
+ * the earliest start and latest end (global nanosecond timer) over all its
+ * warps: trace (device, 2 * n_intervals unsigned 64-bit values) must hold
+ * (UINT64_MAX, 0) per interval before the launch.  Used to balance interval
+ * sizes; HF_ERR_UNSUPPORTED for a 2-way pair instance. */
+hf_status hf_launch_traced(hf_fused f, const void *const *args, int grid, void *stream,
+                           unsigned long long *trace);
+
 /* Launch one kernel alone with `threads` threads per block (the unfused
  * baseline, Sec. 4.1).  Same argument block as in a fused launch; a body run
  * alone on d threads and grid g computes bit-identical results to the same
@@ -363,8 +371,11 @@ typedef struct {
  * loaded interval), gives each interval warps in proportion to its load, and
  * times these plans for block sizes 512 and 1024, register caps none/64/96,
  * and one interval per kernel or about two kernels per interval.  From the
- * fastest it hill-climbs, moving one warp between two intervals while the
- * measured time drops by more than 0.5%, for at most max_evals timed plans.
+ * fastest it rebalances up to six times from a traced launch
+ * (hf_launch_traced), giving interval i warps in proportion to its warps
+ * times its finishing time, then hill-climbs, moving one warp between two
+ * intervals while the measured time drops by more than 0.5%; at most
+ * max_evals timed plans in all.
  * standalone_us (n entries, may be NULL) receives the single-kernel times. */
 hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, int max_evals,
                            int reps, int flush_l2, void *stream, hf_nway_plan *best,

@@ -169,7 +169,7 @@ struct BodyStreamTmpl {
         const int64_t n4 = a.n >> 2;
         const int64_t stride = (int64_t)cx.grid * cx.nthreads;
         const int64_t tiles = (n4 + stride - 1) / stride;
-        const int nslots = a.smem_bytes >> 4;
+        const int nslots = smem_fits(cx, (size_t)a.smem_bytes) ? a.smem_bytes >> 4 : 0;
         const bool staged = cx.tid < nslots;
         const unsigned slot = (unsigned)__cvta_generic_to_shared(cx.smem) + 16u * cx.tid;
         const int k4 = a.k >> 2, kr = a.k & 3, nb = a.n_barriers;

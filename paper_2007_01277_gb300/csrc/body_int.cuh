@@ -48,8 +48,15 @@ struct BodyHist {
 
     static __device__ void run(const Args &a, const Ctx &cx)
     {
-        unsigned *sh = reinterpret_cast<unsigned *>(cx.smem);
         const int nw = cx.nthreads >> 5;
+        if (!smem_fits(cx, (size_t)nw * 256 * sizeof(unsigned))) {
+            // no room for the counter copies: count straight into the bins
+            for (int64_t i = (int64_t)cx.block * cx.nthreads + cx.tid; i < a.n;
+                 i += (int64_t)cx.grid * cx.nthreads)
+                atomicAdd(a.bins + a.x[i], 1u);
+            return;
+        }
+        unsigned *sh = reinterpret_cast<unsigned *>(cx.smem);
         for (int i = cx.tid; i < nw * 256; i += cx.nthreads) sh[i] = 0u;
         interval_sync(cx);
 

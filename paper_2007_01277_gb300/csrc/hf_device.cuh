@@ -24,7 +24,26 @@ struct Ctx {
     int block;           // blockIdx.x
     int grid;            // gridDim.x
     unsigned char *smem; // this interval's slice of dynamic shared memory
+    unsigned smem_end;   // shared-space address one past the slice
 };
+
+// Shared-space address of the start of dynamic shared memory plus its size
+// as launched (the %dynamic_smem_size register).
+__device__ __forceinline__ unsigned dynamic_smem_end(const unsigned char *dyn_base)
+{
+    unsigned sz;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(sz));
+    return (unsigned)__cvta_generic_to_shared(dyn_base) + sz;
+}
+
+// True when `bytes` from the start of the interval's slice were provided by
+// the launch.  Bodies that stage through shared memory check this and take
+// a path without shared memory otherwise, so an under-sized launch can never
+// touch memory outside its allocation.
+__device__ __forceinline__ bool smem_fits(const Ctx &c, size_t bytes)
+{
+    return (size_t)(unsigned)__cvta_generic_to_shared(c.smem) + bytes <= (size_t)c.smem_end;
+}
 
 // The partial barrier of Sec. 3.1: only the d_k threads of this interval
 // arrive.  Intervals are whole warps, so every warp either executes it with

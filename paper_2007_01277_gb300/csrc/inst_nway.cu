@@ -4,7 +4,9 @@
 
 namespace hf {
 
-__global__ void k_nway(const __grid_constant__ NwayParams p) { nway_body(p); }
+// Without an explicit cap the N-way kernel is still bounded so that a
+// 512-thread block always fits (at most 128 registers per thread).
+__global__ void __launch_bounds__(512) k_nway(const __grid_constant__ NwayParams p) { nway_body(p); }
 
 #define HF_NWAY_ENTRY(R) Instance{-1, -1, R, reinterpret_cast<const void *>(&k_nway_cap<R>), nullptr},
 static const Instance kNway[] = {

@@ -39,9 +39,12 @@ __device__ __forceinline__ void single_body(const SingleParams<B> &p)
     c.block = blockIdx.x;
     c.grid = gridDim.x;
     c.smem = hf_smem;
+    c.smem_end = dynamic_smem_end(hf_smem);
     B::run(p.a, c);
 }
 
+// A kernel launched alone, with the registers the compiler picks; block
+// sizes its registers do not allow are refused by the runtime.
 template <class B>
 __global__ void k_single(const __grid_constant__ SingleParams<B> p)
 {
@@ -67,16 +70,19 @@ __device__ __forceinline__ void pair_body(const PairParams<A, B> &p)
     Ctx c;
     c.block = blockIdx.x;
     c.grid = gridDim.x;
+    const unsigned end = dynamic_smem_end(hf_smem);
     if (low) {
         c.tid = threadIdx.x;
         c.nthreads = p.n_low;
         c.bar = 1;
         c.smem = hf_smem;
+        c.smem_end = min(end, (unsigned)__cvta_generic_to_shared(hf_smem) + p.smem_high);
     } else {
         c.tid = threadIdx.x - p.n_low;
         c.nthreads = p.n_high;
         c.bar = 2;
         c.smem = hf_smem + p.smem_high;
+        c.smem_end = end;
     }
     if (low == (p.low_is_a != 0))
         A::run(p.a, c);
@@ -107,8 +113,16 @@ struct NwayParams {
     int sched_body[HF_MAX_SCHEDULE];            // body id of kernel j
     int sched_int[HF_MAX_SCHEDULE];             // interval of kernel j
     unsigned args_off[HF_MAX_SCHEDULE];         // argument block of kernel j in blob
+    unsigned long long *trace;                  // optional: [n_int][2] first start / last end (ns)
     alignas(16) unsigned char blob[kNwayBlob];
 };
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ void dispatch(int body, const unsigned char *args, const Ctx &c)
 {
@@ -151,6 +165,14 @@ __device__ __forceinline__ void nway_body(const NwayParams &p)
     c.block = blockIdx.x;
     c.grid = gridDim.x;
     c.smem = hf_smem + p.smem_off[i];
+    {
+        const unsigned end = dynamic_smem_end(hf_smem);
+        c.smem_end = i + 1 < p.n_int
+                         ? min(end, (unsigned)__cvta_generic_to_shared(hf_smem) + p.smem_off[i + 1])
+                         : end;
+    }
+    const bool lead = p.trace && (threadIdx.x & 31) == 0;
+    if (lead) atomicMin(p.trace + 2 * i, global_ns());
     bool first = true;
     for (int j = 0; j < p.n_sched; ++j) {
         if (p.sched_int[j] != i) continue;
@@ -160,9 +182,10 @@ __device__ __forceinline__ void nway_body(const NwayParams &p)
         first = false;
         dispatch(p.sched_body[j], p.blob + p.args_off[j], c);
     }
+    if (lead) atomicMax(p.trace + 2 * i + 1, global_ns());
 }
 
-__global__ void k_nway(const __grid_constant__ NwayParams p);
+__global__ void __launch_bounds__(512) k_nway(const __grid_constant__ NwayParams p);
 template <int R>
 __global__ void __maxnreg__(R) k_nway_cap(const __grid_constant__ NwayParams p)
 {

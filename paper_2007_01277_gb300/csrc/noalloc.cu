@@ -88,11 +88,18 @@ extern "C" hf_status hf_bn_stats_noalloc(const float *x, float *mean, float *var
     cudaError_t e = cudaMemsetAsync(scratch, 0, BodyBn::counters_bytes(a), st);
     if (e != cudaSuccess) return hf::set_last_error(HF_ERR_CUDA, cudaGetErrorString(e));
 
+    // the body streams its input through a per-warp ring in dynamic shared
+    // memory, sized like every other launch of it
+    const size_t smem = BodyBn::smem_bytes(threads, a);
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(k_bn_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+        return hf::set_last_error(HF_ERR_CUDA, cudaGetErrorString(e));
     if (grid == 0) {
         int dev = 0, sms = 0, per_sm = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
             (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-            (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bn_noalloc, threads, 0)) !=
+            (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bn_noalloc, threads, smem)) !=
                 cudaSuccess)
             return hf::set_last_error(HF_ERR_CUDA, cudaGetErrorString(e));
         if (per_sm <= 0) return hf::set_last_error(HF_ERR_REGS, "block cannot be resident");
@@ -100,7 +107,7 @@ extern "C" hf_status hf_bn_stats_noalloc(const float *x, float *mean, float *var
     }
     hf::SingleParams<BodyBn> p;
     p.a = a;
-    k_bn_noalloc<<<grid, threads, 0, st>>>(p);
+    k_bn_noalloc<<<grid, threads, smem, st>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return hf::set_last_error(HF_ERR_CUDA, cudaGetErrorString(e));
     return HF_OK;

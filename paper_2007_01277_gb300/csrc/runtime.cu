@@ -491,7 +491,24 @@ hf_status hf_fuse_n(const hf_kernel *ks, int n, const int *interval_of, const in
 
 void hf_destroy_fused(hf_fused f) { delete f; }
 
+static hf_status launch_impl(hf_fused f, const void *const *args, int grid, void *stream,
+                             unsigned long long *trace);
+
 hf_status hf_launch(hf_fused f, const void *const *args, int grid, void *stream)
+{
+    return launch_impl(f, args, grid, stream, nullptr);
+}
+
+hf_status hf_launch_traced(hf_fused f, const void *const *args, int grid, void *stream,
+                           unsigned long long *trace)
+{
+    if (!trace) return fail(HF_ERR_INVALID, "NULL trace buffer");
+    if (f && !f->nway) return fail(HF_ERR_UNSUPPORTED, "interval tracing needs an N-way fused kernel");
+    return launch_impl(f, args, grid, stream, trace);
+}
+
+static hf_status launch_impl(hf_fused f, const void *const *args, int grid, void *stream,
+                             unsigned long long *trace)
 {
     if (!f || !args) return fail(HF_ERR_INVALID, "NULL fused kernel or argument list");
     if (grid < 0) return fail(HF_ERR_INVALID, "grid %d", grid);
@@ -519,6 +536,7 @@ hf_status hf_launch(hf_fused f, const void *const *args, int grid, void *stream)
     unsigned smem = 0;
     hf_status s = nway_params(f, args, &p, &smem);
     if (s) return s;
+    p.trace = trace;
     int g = 0;
     s = pick_grid(f->inst->func, f->d0, smem, grid, &g, nullptr);
     if (s) return s;

@@ -314,7 +314,71 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
                 if (st) return st;
             }
     if (best_t < 0.f) return HF_ERR_INVALID;
-    // 3. hill climb: move one warp between two intervals while it helps
+    // 3. rebalance from measured interval finishing times: interval i gets
+    //    warps in proportion to warps_i * finish_i, so that intervals that
+    //    end early give warps to the ones that end late
+    unsigned long long *d_trace = nullptr;
+    if (cudaMalloc(&d_trace, 2 * HF_MAX_INTERVALS * sizeof(unsigned long long)) != cudaSuccess)
+        return HF_ERR_CUDA;
+    for (int round = 0; round < 6 && evals < max_evals; ++round) {
+        const NwayPlanC base = bp;
+        int thr[HF_MAX_INTERVALS];
+        for (int i = 0; i < base.P; ++i) thr[i] = 32 * base.warps[i];
+        hf_fused f = nullptr;
+        if (hf_fuse_n(ks, n, base.io, thr, base.P, base.cap, &f)) break;
+        unsigned long long h[2 * HF_MAX_INTERVALS];
+        for (int i = 0; i < base.P; ++i) h[2 * i] = ~0ull, h[2 * i + 1] = 0ull;
+        cudaStream_t cs = static_cast<cudaStream_t>(stream);
+        bool ok = cudaMemcpyAsync(d_trace, h, sizeof h, cudaMemcpyHostToDevice, cs) == cudaSuccess &&
+                  hf_launch_traced(f, args, best->grid, stream, d_trace) == HF_OK &&
+                  cudaMemcpyAsync(h, d_trace, sizeof h, cudaMemcpyDeviceToHost, cs) == cudaSuccess &&
+                  cudaStreamSynchronize(cs) == cudaSuccess;
+        hf_destroy_fused(f);
+        if (!ok) {
+            cudaFree(d_trace);
+            return HF_ERR_CUDA;
+        }
+        unsigned long long t0 = ~0ull;
+        for (int i = 0; i < base.P; ++i) t0 = std::min(t0, h[2 * i]);
+        const int W = [&] { int w = 0; for (int i = 0; i < base.P; ++i) w += base.warps[i]; return w; }();
+        double want[HF_MAX_INTERVALS], tot = 0.0;
+        for (int i = 0; i < base.P; ++i) {
+            want[i] = base.warps[i] * (double)(h[2 * i + 1] - t0);
+            tot += want[i];
+        }
+        if (tot <= 0.0) break;
+        NwayPlanC p = base;
+        int used = 0;
+        for (int i = 0; i < base.P; ++i) {
+            p.warps[i] = std::max(1, (int)(want[i] / tot * W));
+            used += p.warps[i];
+        }
+        while (used < W) {   // hand out the remainder to the latest finishers
+            int bi = 0;
+            for (int i = 1; i < p.P; ++i)
+                if (want[i] / p.warps[i] > want[bi] / p.warps[bi]) bi = i;
+            ++p.warps[bi];
+            ++used;
+        }
+        while (used > W) {
+            int bi = -1;
+            for (int i = 0; i < p.P; ++i)
+                if (p.warps[i] > 1 && (bi < 0 || want[i] / p.warps[i] < want[bi] / p.warps[bi])) bi = i;
+            if (bi < 0) break;
+            --p.warps[bi];
+            --used;
+        }
+        if (std::equal(p.warps, p.warps + p.P, base.warps)) break;
+        const float before = best_t;
+        st = consider(p);
+        if (st) {
+            cudaFree(d_trace);
+            return st;
+        }
+        if (!(best_t < before)) break;
+    }
+    cudaFree(d_trace);
+    // 4. hill climb: move one warp between two intervals while it helps
     bool improved = true;
     while (improved && evals < max_evals) {
         improved = false;

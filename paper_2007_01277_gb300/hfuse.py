@@ -162,6 +162,7 @@ def _load():
         "hf_mlp_train": (_i32, [_P, _P, _P, _P, _P, _P, _i32, _i32, _f32, _f32, _f32, _f32, _i32,
                                 _P, _P, _P]),
         "hf_mlp_nparams": (_i32, []),
+        "hf_launch_traced": (_i32, [_P, ctypes.POINTER(_P), _i32, _P, _P]),
         "hf_graph_begin": (_i32, [_P]),
         "hf_graph_end": (_i32, [_P, ctypes.POINTER(_P)]),
         "hf_graph_launch": (_i32, [_P, _P]),
@@ -457,3 +458,17 @@ def hf_mlp_train(params, m, v, X, Y, idx, steps, batch, lr=1e-3, beta1=0.9, beta
     _check("hf_mlp_train", lib.hf_mlp_train(_ptr(params), _ptr(m), _ptr(v), _ptr(X), _ptr(Y),
                                             _ptr(idx), steps, batch, lr, beta1, beta2, eps, t0,
                                             _ptr(loss_out), _ptr(grad_out), _stream_ptr(stream)))
+
+
+def hf_launch_traced(f, args, grid=0, stream=None):
+    """hf_launch of an N-way fused kernel that returns per-interval
+    (start, end) in nanoseconds of the global timer."""
+    import torch
+    n_int = 15
+    tr = torch.zeros(2 * n_int, dtype=torch.int64, device="cuda")
+    tr[0::2] = -1   # all ones: the unsigned maximum
+    _check("hf_launch_traced", lib.hf_launch_traced(f, _argv(args), grid, _stream_ptr(stream),
+                                                    tr.data_ptr()))
+    torch.cuda.synchronize()
+    h = tr.cpu().numpy().view("uint64")
+    return [(int(h[2 * i]), int(h[2 * i + 1])) for i in range(n_int) if h[2 * i + 1] > 0]
