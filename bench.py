@@ -144,7 +144,7 @@ def _mb(n):
 
 PAIR_SPECS = {
     # bilinear x2 of 32x64x128x128 + 3x3/s2/p1 max pool of 32x128x112x112
-    "upsample_maxpool": dict(d0=512, splits=(128, 256, 384), caps=(0, 64, 96), bps=(1, 2, 3),
+    "upsample_maxpool": dict(d0=512, splits=(128, 256, 384), caps=(0, 40, 48, 64, 96), bps=(1, 2, 3),
                              flush=False, name="fused_upsample_maxpool",
                              desc=WORKLOAD),
     # 2^28-byte histogram + 2^26 Philox4x32-10 blocks
@@ -603,7 +603,7 @@ def main():
                     choices=sorted(PAIR_SPECS) + ["nway8", "cost_model"])
     ap.add_argument("--cost-db", default=None)
     ap.add_argument("--cost-steps", type=int, default=20000)
-    ap.add_argument("--nway-evals", type=int, default=120)
+    ap.add_argument("--nway-evals", type=int, default=200)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

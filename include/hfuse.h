@@ -369,7 +369,8 @@ typedef struct {
 /* Autotuner for N-way fusion.  Times every kernel alone (256 threads), then
  * packs kernels onto intervals longest-first (LPT: each goes to the least
  * loaded interval), gives each interval warps in proportion to its load, and
- * times these plans for block sizes 512 and 1024, register caps none/64/96,
+ * times these plans for block sizes 512, 768 and 1024, register caps
+ * none/40/48/64/96,
  * and one interval per kernel or about two kernels per interval.  From the
  * fastest it rebalances up to six times from a traced launch
  * (hf_launch_traced), giving interval i warps in proportion to its warps

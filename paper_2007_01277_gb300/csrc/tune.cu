@@ -279,8 +279,8 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
     std::vector<int> order(n);
     for (int k = 0; k < n; ++k) order[k] = k;
     std::sort(order.begin(), order.end(), [&](int a, int b) { return t[a] > t[b]; });
-    const int d0s[] = {512, 1024};
-    const int caps[] = {0, 64, 96};
+    const int d0s[] = {512, 768, 1024};
+    const int caps[] = {0, 40, 48, 64, 96};
     for (int d0 : d0s)
         for (int cap : caps)
             for (int P : {n, (n + 1) / 2}) {
