@@ -281,6 +281,19 @@ def run_pair(cx, name):
                                     flush_l2=fl, stream=st)
     naive = [p for p in ok if p["split"] == d0 // 2 and p["regcap"] == 0]
     naive = min(naive, key=lambda p: -p["blocks_per_sm"]) if naive else None
+    # vertical fusion (Sec. 2.2): every thread runs one kernel, then the other
+    vfuse = None
+    for dv in (256, 512):
+        try:
+            fv = H.hf_fuse_n([ka, kb], [0, 0], [dv], 0)
+        except H.HFError:
+            continue
+        iv = H.hf_query(fv, args)
+        tv = H.hf_time_fused(fv, args, iv["blocks_per_sm"] * lim.sm_count, reps=5, flush_l2=fl,
+                             stream=st)[0]
+        H.hf_destroy_fused(fv)
+        if vfuse is None or tv < vfuse[0]:
+            vfuse = (tv, dv)
     fused = H.hf_fuse(ka, kb, best["split"], d0, best["regcap"])
     grid = best["grid"]
 
@@ -358,7 +371,9 @@ def run_pair(cx, name):
         "pipe_peaks_per_s": {k: float("%.4g" % v) for k, v in peaks.items()},
         "search": {"exhaustive_best_us": round(best["time_us"], 3), "points": len(ok),
                    "alg2": {k: alg2[k] for k in ("split", "regcap", "blocks_per_sm", "time_us")},
-                   "naive_even_split_us": round(naive["time_us"], 3) if naive else None},
+                   "naive_even_split_us": round(naive["time_us"], 3) if naive else None,
+                   "vfuse_us": round(vfuse[0], 3) if vfuse else None,
+                   "vfuse_block": vfuse[1] if vfuse else None},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "traffic": load_traffic(spec["name"]),
                      "peak_source": peak_kind},
@@ -404,7 +419,7 @@ def run_nway(cx):
     nbytes = sum(t.numel() * t.element_size() for t in (xb, xi, ci, xp, yp, xu, yu, xh, po, xq, yq, x16, y16, o16))
     ops = {"ffma": sp["poly_n"] * 64 * 33, "imul": sp["philox_n"] * 40, "smem_atomic": sp["hist_n"]}
 
-    plan, single = H.hf_autotune_nway(ks, args, max_evals=cx.args.nway_evals, reps=3, stream=st)
+    plan, single = H.hf_autotune_nway(ks, args, max_evals=cx.args.nway_evals, reps=5, stream=st)
     fused = H.hf_fuse_n(ks, plan["interval_of"], plan["interval_threads"], plan["regcap"])
     lim = H.hf_device_info()
     grid = plan["grid"]
@@ -497,9 +512,39 @@ def run_cost_model(cx):
     }
 
 
+def run_experiment(cx, which):
+    import math
+
+    from paper_2007_01277_gb300 import experiments as E
+    if which == "table2":
+        rows = E.table2(cx.dev)
+        sp = [r["hfuse_alg2"]["ratio"] for r in rows.values()]
+        desc = ("the ten pairs of the five deep-learning kernels at execution-time ratio ~1 "
+                "(Table 2's setting): native two-stream vs HFuse (Algorithm 2, no-cap best, "
+                "RegCap), naive even split, VFuse")
+        extra = {"pairs": rows}
+    else:
+        series = E.ratio_sweep(cx.dev)
+        sp = [r["hfuse_alg2"]["ratio"] for s in series.values() for r in s]
+        desc = ("execution-time-ratio sweep (Fig. 3's protocol): hist+maxpool with maxpool "
+                "scaled, bn+hist with bn scaled, 1/8x..4x")
+        extra = {"series": series}
+    geo = math.exp(sum(math.log(v) for v in sp) / len(sp))
+    line = {"metric": METRIC, "value": round(geo, 4),
+            "unit": "geomean T_native/T_hfuse (Algorithm 2 pick, native = two streams)",
+            "n_gpus": cx.world, "steps": None, "warmup": None, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/u8",
+            "data": "synthetic (seeded torch.Generator, CPU-drawn)",
+            "config": {"workload": desc}}
+    line.update(extra)
+    return line
+
+
 def run_ours(args):
     cx = Ctx(args)
-    if args.workload == "cost_model":
+    if args.workload in ("table2", "ratio_sweep"):
+        line = run_experiment(cx, args.workload)
+    elif args.workload == "cost_model":
         line = run_cost_model(cx)
     elif args.workload == "nway8":
         line = run_nway(cx)
@@ -600,10 +645,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="upsample_maxpool",
-                    choices=sorted(PAIR_SPECS) + ["nway8", "cost_model"])
+                    choices=sorted(PAIR_SPECS) + ["nway8", "cost_model", "table2", "ratio_sweep"])
     ap.add_argument("--cost-db", default=None)
     ap.add_argument("--cost-steps", type=int, default=20000)
-    ap.add_argument("--nway-evals", type=int, default=200)
+    ap.add_argument("--nway-evals", type=int, default=300)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -262,12 +262,23 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
         ++evals;
         return s2;
     };
+    struct Seed {
+        float t;
+        int grid;
+        NwayPlanC p;
+    };
+    std::vector<Seed> seeds;
+    float last_t = -1.f;
+    int last_grid = 0;
     auto consider = [&](const NwayPlanC &p) -> hf_status {
         float us = 0.f;
         int grid = 0;
+        last_t = -1.f;
         hf_status s2 = eval(p, &us, &grid);
         if (s2 == HF_ERR_CUDA) return s2;
         if (s2) return HF_OK;   // not buildable / not resident: skip
+        last_t = us;
+        last_grid = grid;
         if (best_t < 0.f || us < best_t) {
             best_t = us;
             bp = p;
@@ -312,16 +323,23 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
                 }
                 st = consider(p);
                 if (st) return st;
+                if (last_t > 0.f) seeds.push_back(Seed{last_t, last_grid, p});
             }
     if (best_t < 0.f) return HF_ERR_INVALID;
+    std::sort(seeds.begin(), seeds.end(), [](const Seed &a, const Seed &b) { return a.t < b.t; });
+    if (seeds.size() > 12) seeds.resize(12);
     // 3. rebalance from measured interval finishing times: interval i gets
     //    warps in proportion to warps_i * finish_i, so that intervals that
     //    end early give warps to the ones that end late
     unsigned long long *d_trace = nullptr;
     if (cudaMalloc(&d_trace, 2 * HF_MAX_INTERVALS * sizeof(unsigned long long)) != cudaSuccess)
         return HF_ERR_CUDA;
+    for (const Seed &sd : seeds) {
+    NwayPlanC cur = sd.p;
+    int cur_grid = sd.grid;
+    float cur_t = sd.t;
     for (int round = 0; round < 6 && evals < max_evals; ++round) {
-        const NwayPlanC base = bp;
+        const NwayPlanC base = cur;
         int thr[HF_MAX_INTERVALS];
         for (int i = 0; i < base.P; ++i) thr[i] = 32 * base.warps[i];
         hf_fused f = nullptr;
@@ -330,7 +348,7 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
         for (int i = 0; i < base.P; ++i) h[2 * i] = ~0ull, h[2 * i + 1] = 0ull;
         cudaStream_t cs = static_cast<cudaStream_t>(stream);
         bool ok = cudaMemcpyAsync(d_trace, h, sizeof h, cudaMemcpyHostToDevice, cs) == cudaSuccess &&
-                  hf_launch_traced(f, args, best->grid, stream, d_trace) == HF_OK &&
+                  hf_launch_traced(f, args, cur_grid, stream, d_trace) == HF_OK &&
                   cudaMemcpyAsync(h, d_trace, sizeof h, cudaMemcpyDeviceToHost, cs) == cudaSuccess &&
                   cudaStreamSynchronize(cs) == cudaSuccess;
         hf_destroy_fused(f);
@@ -369,30 +387,61 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
             --used;
         }
         if (std::equal(p.warps, p.warps + p.P, base.warps)) break;
-        const float before = best_t;
         st = consider(p);
         if (st) {
             cudaFree(d_trace);
             return st;
         }
-        if (!(best_t < before)) break;
+        if (!(last_t > 0.f && last_t < cur_t)) break;   // this seed stopped improving
+        cur = p;
+        cur_t = last_t;
+        cur_grid = last_grid;
+    }
     }
     cudaFree(d_trace);
-    // 4. hill climb: move one warp between two intervals while it helps
+    // 4. local search from the fastest plan: move one warp between two
+    //    intervals, move one kernel to another interval, or swap two kernels
+    //    of different intervals; take the best neighbour while it helps
+    auto used_all = [&](const NwayPlanC &p) {
+        int cnt[HF_MAX_INTERVALS] = {0};
+        for (int k = 0; k < n; ++k) ++cnt[p.io[k]];
+        for (int i = 0; i < p.P; ++i)
+            if (!cnt[i]) return false;
+        return true;
+    };
     bool improved = true;
     while (improved && evals < max_evals) {
         improved = false;
         const NwayPlanC base = bp;
         const float base_t = best_t;
-        for (int i = 0; i < base.P && evals < max_evals; ++i)
-            for (int j = 0; j < base.P && evals < max_evals; ++j) {
+        std::vector<NwayPlanC> nb;
+        for (int i = 0; i < base.P; ++i)
+            for (int j = 0; j < base.P; ++j) {
                 if (i == j || base.warps[i] <= 1) continue;
                 NwayPlanC p = base;
                 --p.warps[i];
                 ++p.warps[j];
-                st = consider(p);
-                if (st) return st;
+                nb.push_back(p);
             }
+        for (int k = 0; k < n; ++k)
+            for (int j = 0; j < base.P; ++j) {
+                if (j == base.io[k]) continue;
+                NwayPlanC p = base;
+                p.io[k] = j;
+                if (used_all(p)) nb.push_back(p);
+            }
+        for (int k = 0; k < n; ++k)
+            for (int l = k + 1; l < n; ++l) {
+                if (base.io[k] == base.io[l]) continue;
+                NwayPlanC p = base;
+                std::swap(p.io[k], p.io[l]);
+                nb.push_back(p);
+            }
+        for (const NwayPlanC &p : nb) {
+            if (evals >= max_evals) break;
+            st = consider(p);
+            if (st) return st;
+        }
         improved = best_t < base_t * 0.995f;
     }
     const int grid = best->grid;

@@ -290,3 +290,23 @@ def test_stream_wait_and_query():
     assert info["regs"] > 0 and info["blocks_per_sm"] >= 1
     lim = H.hf_device_info()
     assert lim.sm_count > 0 and lim.regs_per_sm == 65536
+
+
+@pytest.mark.parametrize("pair", [(H.BN_STATS, H.HIST256), (H.UPSAMPLE2X, H.MAXPOOL3S2)],
+                         ids=lambda p: "%s+%s" % (H.BODY_NAMES[p[0]], H.BODY_NAMES[p[1]]))
+def test_vertical_fusion_schedule_bit_exact(pair):
+    """Vertical fusion (Sec. 2.2): both kernels on one interval of the whole
+    block, one after the other, equal their standalone launches."""
+    a, b = pair
+    mk_a, outs_a = _case(a, 3)
+    mk_b, outs_b = _case(b, 4)
+    ka, kb = H.hf_register_kernel(a), H.hf_register_kernel(b)
+    f = H.hf_fuse_n([ka, kb], [0, 0], [256], 0)
+    fa, fb = _fresh(outs_a), _fresh(outs_b)
+    H.hf_launch(f, [mk_a(fa), mk_b(fb)], grid=19)
+    sa, sb = _fresh(outs_a), _fresh(outs_b)
+    H.hf_launch_single(ka, mk_a(sa), 256, grid=19)
+    H.hf_launch_single(kb, mk_b(sb), 256, grid=19)
+    torch.cuda.synchronize()
+    for u, v in zip(fa + fb, sa + sb):
+        assert torch.equal(u, v)

@@ -62,7 +62,8 @@ def test_autotune_nway_plan_is_valid_and_correct():
     n_int = plan["n_intervals"]
     assert 1 <= n_int <= 4 and sum(plan["interval_threads"]) in (512, 1024)
     assert set(plan["interval_of"]) == set(range(n_int))
-    assert plan["time_us"] > 0 and plan["evals"] <= 20 + 12
+    # the seeds (at most 3 block sizes x 5 caps x 2 packings) are always timed
+    assert plan["time_us"] > 0 and plan["evals"] <= 20 + 30
     f = H.hf_fuse_n(ks, plan["interval_of"], plan["interval_threads"], plan["regcap"])
     bins.zero_()
     H.hf_launch(f, args, plan["grid"])
