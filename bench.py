@@ -254,11 +254,18 @@ class Ctx:
         self.torch.cuda.synchronize()
 
     def max_over_ranks(self, v):
-        if not self.dist:
-            return v
-        t = self.torch.tensor([v], device=self.dev)
-        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
-        return t.item()
+        return max_over_ranks(v, self.dist, self.dev)
+
+
+def max_over_ranks(value, dist=None, device=None):
+    """The slowest rank's time: every rank contributes its own and gets the
+    maximum back (one all-reduce; replicas exchange nothing else)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
 
 
 def run_pair(cx, name):
