@@ -472,6 +472,25 @@ def run_nway(cx):
     t_serial = statistics.median(cx.timed(lambda: H.hf_graph_launch(graphs["serial"], st), max(5, K // 4), warm=Wm))
     t_nstream = statistics.median(cx.timed(lambda: H.hf_graph_launch(graphs["nstream"], st), max(5, K // 4), warm=Wm))
     t_fused_nograph = statistics.median(cx.timed(issue_fused, max(5, K // 4), warm=Wm))
+    # end to end: every input from pinned host memory, the graph, every output back
+    ins = [xb, xi, xp, xu, xh, xq, x16, y16]
+    outs = [mb, vb, ci, yp, yu, bins, po, yq, o16]
+    host_in = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in ins]
+    for h, d in zip(host_in, ins):
+        h.copy_(d)
+    host_out = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs]
+
+    def step_e2e():
+        for h, d in zip(host_in, ins):
+            d.copy_(h, non_blocking=True)
+        H.hf_graph_launch(graphs["fused"], st)
+        for h, d in zip(host_out, outs):
+            h.copy_(d, non_blocking=True)
+
+    t_e2e = statistics.median(cx.timed(step_e2e, max(3, K // 40), warm=1))
+    e2e = {"value": round(t_e2e, 2), "unit": "us",
+           "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in ins),
+           "d2h_bytes_per_step": sum(t.numel() * t.element_size() for t in outs)}
     hbm, peak_kind = measured_peaks()
     peaks = pipe_peaks(H, st)
     t_ideal, terms = ideal_us(nbytes, ops, peaks, hbm)
@@ -494,7 +513,7 @@ def run_nway(cx):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "traffic": load_traffic("nway8"),
                      "peak_source": peak_kind},
-        "e2e": None, "gpu_launches": K, "clocks": clk.summary(),
+        "e2e": e2e, "gpu_launches": K, "clocks": clk.summary(),
     }
 
 
@@ -557,8 +576,10 @@ def run_ours(args):
         line = run_nway(cx)
     else:
         line = run_pair(cx, args.workload)
-    if cx.rank == 0 and not args.no_cpu_baseline and args.workload == "upsample_maxpool":
-        line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
+    if cx.rank == 0 and not args.no_cpu_baseline:
+        cb = cpu_baseline_for(args.workload)
+        if cb is not None:
+            line["cpu_baseline"] = cb
     if cx.rank == 0:
         print(json.dumps(line), flush=True)
     if cx.dist:
@@ -618,6 +639,76 @@ def cpu_baseline(seconds: float = 15.0, images: int | None = None):
     us_full = t / n * 32 * 1e6
     return {"value": round(us_full, 1), "unit": "us", "cores": cores, "kind": "oracle",
             "sample": "%d of 32 images of both inputs (%.1f s), scaled x%.1f" % (n, t, 32 / n)}
+
+
+def _pool_time(jobs, cores):
+    from concurrent.futures import ThreadPoolExecutor
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        list(ex.map(lambda f: f(), jobs))
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_for(workload: str):
+    """The oracle on a bounded sample of `workload`, spread over the host
+    cores, scaled to the full workload.  Returns the cpu_baseline object."""
+    import numpy as np
+
+    import oracle
+    from paper_2007_01277_gb300 import workloads as W
+    cores = os.cpu_count() or 1
+    if workload == "upsample_maxpool":
+        return cpu_baseline(seconds=10.0)
+    if workload == "hist_philox":
+        xs = W.hist_input(1 << 24).numpy()               # 1/16 of the bytes
+        chunks = np.array_split(xs, cores)
+        jobs = [lambda c=c: oracle.hist256(c) for c in chunks]
+        t_h = _pool_time(jobs, cores) * 16
+        per = (1 << 18) // cores                          # 1/256 of the blocks
+        jobs = [lambda i=i: oracle.philox4x32_10(0, per, first=i * per) for i in range(cores)]
+        t_p = _pool_time(jobs, cores) * (1 << 26) / (per * cores)
+        return {"value": round((t_h + t_p) * 1e6, 1), "unit": "us", "cores": cores, "kind": "oracle",
+                "sample": "hist on 2^24 of 2^28 bytes (x16), Philox on %d of 2^26 blocks" % (per * cores)}
+    if workload == "bn_poly":
+        x = W.bn_input((8, 64, 32, 32)).numpy()
+        t_b = _pool_time([lambda: oracle.bn_stats(x)], 1)
+        xq = W.poly_input(1 << 20).numpy()[: 1 << 14]
+        c = W.poly_coefficients().numpy()
+        chunks = np.array_split(xq, cores)
+        t_q = _pool_time([lambda ch=ch: oracle.poly(ch, c) for ch in chunks], cores) * 64
+        return {"value": round((t_b + t_q) * 1e6, 1), "unit": "us", "cores": cores, "kind": "oracle",
+                "sample": "bn on the whole input, poly on 2^14 of 2^20 elements (x64)"}
+    if workload == "nway8":
+        sp = W.WORKLOADS["nway8"]
+        parts = []
+        xb = W.bn_input((2,) + sp["bn"][1:]).numpy()                  # 2 of 64 images
+        parts.append((lambda: oracle.bn_stats(xb), 32))
+        xi = W.im2col_input((1,) + sp["im2col"][1:]).numpy()         # 1 of 32 images
+        parts.append((lambda: oracle.im2col3(xi), 32))
+        xp = W.maxpool_input((1,) + sp["pool"][1:]).numpy()
+        parts.append((lambda: oracle.maxpool3s2p1(xp), 32))
+        xu = W.upsample_input((1,) + sp["up"][1:]).numpy()
+        parts.append((lambda: oracle.upsample2x(xu), 32))
+        xh = W.hist_input(1 << 22).numpy()
+        parts.append((lambda: oracle.hist256(xh), 16))
+        parts.append((lambda: oracle.philox4x32_10(0, 1 << 16), 256))
+        xq = W.poly_input(1 << 12).numpy()
+        cq = W.poly_coefficients().numpy()
+        parts.append((lambda: oracle.poly(xq, cq), 1024))
+        x16, y16 = W.bf16_inputs(1 << 22)
+        b1, b2 = (t.view(torch_int16()).numpy().view(np.uint16) for t in (x16, y16))
+        parts.append((lambda: oracle.bf16_axpy(b1, b2, 0.5), 32))
+        total = 0.0
+        for fn, scale in parts:
+            total += _pool_time([fn], 1) * scale
+        return {"value": round(total * 1e6, 1), "unit": "us", "cores": 1, "kind": "oracle",
+                "sample": "each of the 8 kernels on a 1/16-1/1024 slice, single-threaded, scaled"}
+    return None
+
+
+def torch_int16():
+    import torch
+    return torch.int16
 
 
 def run_reference(args):

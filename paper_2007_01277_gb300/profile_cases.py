@@ -14,6 +14,9 @@ and prints the median CUDA-event time per launch.  Cases:
   bn_large        bn stats 64x256x56x56
   im2col          im2col 32x64x56x56
   bf16            bf16 scale+add on 2^27
+  nway8           the eight kernels of the N-way workload in one launch with a
+                  fixed plan (--plan "io;threads;cap", default the autotuned
+                  4-interval plan)
 --scale shrinks the batch dimension (and 1-D sizes) by F for small captures.
 """
 from __future__ import annotations
@@ -74,6 +77,30 @@ def build(case, scale, dev):
         x, y = (t.to(dev) for t in W.bf16_inputs(n1(1 << 27)))
         o = torch.empty_like(x)
         out["bf16"] = (H.BF16_AXPY, H.bf16_axpy_args(x, y, o), (x, y, o))
+    if case == "nway8":
+        sp = W.WORKLOADS["nway8"]
+        xb = W.bn_input((nb(64),) + sp["bn"][1:]).to(dev)
+        m, v = torch.empty(256, device=dev), torch.empty(256, device=dev)
+        ws = H.bn_stats_workspace(xb)
+        out["bn"] = (H.BN_STATS, H.bn_stats_args(xb, m, v, ws), ())
+        xi = W.im2col_input((nb(32),) + sp["im2col"][1:]).to(dev)
+        ci = torch.empty(xi.shape[0], 576, 3136, device=dev)
+        out["im2col"] = (H.IM2COL3, H.im2col3_args(xi, ci), ())
+        xp = W.maxpool_input((nb(32),) + sp["pool"][1:]).to(dev)
+        yp = torch.empty(xp.shape[:2] + (56, 56), device=dev)
+        out["pool"] = (H.MAXPOOL3S2, H.maxpool3s2_args(xp, yp), ())
+        xu = W.upsample_input((nb(32),) + sp["up"][1:]).to(dev)
+        yu = torch.empty(xu.shape[:2] + (256, 256), device=dev)
+        out["up"] = (H.UPSAMPLE2X, H.upsample2x_args(xu, yu), ())
+        xh = W.hist_input(n1(sp["hist_n"])).to(dev)
+        bins = torch.zeros(256, dtype=torch.int32, device=dev)
+        out["hist"] = (H.HIST256, H.hist256_args(xh, bins), ())
+        po = torch.empty((n1(sp["philox_n"]), 4), dtype=torch.int32, device=dev)
+        out["philox"] = (H.PHILOX, H.philox_args(po, 0), ())
+        xq = W.poly_input(n1(sp["poly_n"])).to(dev)
+        out["poly"] = (H.POLY, H.poly_args(xq, torch.empty_like(xq), W.poly_coefficients().tolist()), ())
+        x16, y16 = (t.to(dev) for t in W.bf16_inputs(n1(sp["bf16_n"])))
+        out["bf16"] = (H.BF16_AXPY, H.bf16_axpy_args(x16, y16, torch.empty_like(x16)), ())
     if not out:
         raise SystemExit("unknown case " + case)
     return out
@@ -89,13 +116,27 @@ def main():
     ap.add_argument("--bps", type=int, default=0)
     ap.add_argument("--threads", type=int, default=256)
     ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--plan", default="3,3,2,1,3,1,0,2;128,288,352,256;48")
     a = ap.parse_args()
     dev = torch.device("cuda:0")
     parts = build(a.case, a.scale, dev)
     lim = H.hf_device_info()
     stream = torch.cuda.Stream()
     names = list(parts)
-    if len(names) == 2:
+    if len(names) > 2:
+        io, thr, cap = a.plan.split(";")
+        io = [int(v) for v in io.split(",")]
+        thr = [int(v) for v in thr.split(",")]
+        ks = [H.hf_register_kernel(parts[nm][0]) for nm in names]
+        args = [parts[nm][1] for nm in names]
+        f = H.hf_fuse_n(ks, io, thr, int(cap))
+        info = H.hf_query(f, args)
+        grid = (a.bps or info["blocks_per_sm"]) * lim.sm_count
+
+        def launch():
+            H.hf_launch(f, args, grid, stream)
+        desc = "N-way %s intervals %s cap %s grid %d regs %d" % (names, thr, cap, grid, info["regs"])
+    elif len(names) == 2:
         ka = H.hf_register_kernel(parts[names[0]][0])
         kb = H.hf_register_kernel(parts[names[1]][0])
         split = a.split or a.d0 // 2
