@@ -746,7 +746,7 @@ def main():
                     choices=sorted(PAIR_SPECS) + ["nway8", "cost_model", "table2", "ratio_sweep"])
     ap.add_argument("--cost-db", default=None)
     ap.add_argument("--cost-steps", type=int, default=20000)
-    ap.add_argument("--nway-evals", type=int, default=300)
+    ap.add_argument("--nway-evals", type=int, default=800)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

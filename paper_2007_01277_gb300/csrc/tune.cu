@@ -267,7 +267,7 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
         int grid;
         NwayPlanC p;
     };
-    std::vector<Seed> seeds;
+    std::vector<Seed> seeds, seen;
     float last_t = -1.f;
     int last_grid = 0;
     auto consider = [&](const NwayPlanC &p) -> hf_status {
@@ -279,6 +279,7 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
         if (s2) return HF_OK;   // not buildable / not resident: skip
         last_t = us;
         last_grid = grid;
+        seen.push_back(Seed{us, grid, p});
         if (best_t < 0.f || us < best_t) {
             best_t = us;
             bp = p;
@@ -409,40 +410,81 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
             if (!cnt[i]) return false;
         return true;
     };
-    bool improved = true;
-    while (improved && evals < max_evals) {
-        improved = false;
-        const NwayPlanC base = bp;
-        const float base_t = best_t;
-        std::vector<NwayPlanC> nb;
-        for (int i = 0; i < base.P; ++i)
-            for (int j = 0; j < base.P; ++j) {
-                if (i == j || base.warps[i] <= 1) continue;
+    // local search from each of the three fastest distinct plans seen so far
+    std::sort(seen.begin(), seen.end(), [](const Seed &a, const Seed &b) { return a.t < b.t; });
+    std::vector<NwayPlanC> starts;
+    auto same = [&](const NwayPlanC &a, const NwayPlanC &b) {
+        if (a.P != b.P || a.cap != b.cap) return false;
+        for (int k = 0; k < n; ++k)
+            if (a.io[k] != b.io[k]) return false;
+        for (int i = 0; i < a.P; ++i)
+            if (a.warps[i] != b.warps[i]) return false;
+        return true;
+    };
+    for (const Seed &sd : seen) {
+        bool dup = false;
+        for (const NwayPlanC &q : starts) dup = dup || same(q, sd.p);
+        if (!dup) starts.push_back(sd.p);
+        if (starts.size() == 3) break;
+    }
+    for (const NwayPlanC &start : starts) {
+        NwayPlanC cur = start;
+        float cur_t = -1.f;
+        for (const Seed &sd : seen)
+            if (same(sd.p, start)) {
+                cur_t = sd.t;
+                break;
+            }
+        bool improved = true;
+        while (improved && evals < max_evals) {
+            improved = false;
+            const NwayPlanC base = cur;
+            std::vector<NwayPlanC> nb;
+            for (int i = 0; i < base.P; ++i)
+                for (int j = 0; j < base.P; ++j) {
+                    if (i == j || base.warps[i] <= 1) continue;
+                    NwayPlanC p = base;
+                    --p.warps[i];
+                    ++p.warps[j];
+                    nb.push_back(p);
+                }
+            for (int k = 0; k < n; ++k)
+                for (int j = 0; j < base.P; ++j) {
+                    if (j == base.io[k]) continue;
+                    NwayPlanC p = base;
+                    p.io[k] = j;
+                    if (used_all(p)) nb.push_back(p);
+                }
+            for (int k = 0; k < n; ++k)
+                for (int l = k + 1; l < n; ++l) {
+                    if (base.io[k] == base.io[l]) continue;
+                    NwayPlanC p = base;
+                    std::swap(p.io[k], p.io[l]);
+                    nb.push_back(p);
+                }
+            for (int cap : caps) {   // same plan under another register cap
+                if (cap == base.cap) continue;
                 NwayPlanC p = base;
-                --p.warps[i];
-                ++p.warps[j];
+                p.cap = cap;
                 nb.push_back(p);
             }
-        for (int k = 0; k < n; ++k)
-            for (int j = 0; j < base.P; ++j) {
-                if (j == base.io[k]) continue;
-                NwayPlanC p = base;
-                p.io[k] = j;
-                if (used_all(p)) nb.push_back(p);
+            float step_t = cur_t;
+            NwayPlanC step_p = cur;
+            for (const NwayPlanC &p : nb) {
+                if (evals >= max_evals) break;
+                st = consider(p);
+                if (st) return st;
+                if (last_t > 0.f && (step_t < 0.f || last_t < step_t)) {
+                    step_t = last_t;
+                    step_p = p;
+                }
             }
-        for (int k = 0; k < n; ++k)
-            for (int l = k + 1; l < n; ++l) {
-                if (base.io[k] == base.io[l]) continue;
-                NwayPlanC p = base;
-                std::swap(p.io[k], p.io[l]);
-                nb.push_back(p);
+            if (step_t > 0.f && (cur_t < 0.f || step_t < cur_t * 0.995f)) {
+                cur = step_p;
+                cur_t = step_t;
+                improved = true;
             }
-        for (const NwayPlanC &p : nb) {
-            if (evals >= max_evals) break;
-            st = consider(p);
-            if (st) return st;
         }
-        improved = best_t < base_t * 0.995f;
     }
     const int grid = best->grid;
     std::memset(best, 0, sizeof *best);
