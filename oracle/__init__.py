@@ -25,6 +25,16 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
   mlp           finite differences and torch autograd in float64
   register_bound / blocks_per_sm   the worked example of Sec. 2.1
   alg2_search   brute-force argmin over the same table
+  sha256 / sha256d_scan     hashlib.sha256 (applied twice for the scan)
+  blake2b / blake2b_scan    hashlib.blake2b
+  blake2s       hashlib.blake2s; pins the 32-bit rounds BLAKE-256 shares
+  blake256 / blake256_scan  rounds and sigma table pinned through blake2s,
+                the pi constants through mpmath; the BLAKE-256 framing
+                (constant XOR, counter words, padding) is "parity unpinned":
+                no published test vector is within reach
+  hash constants  square and cube roots of primes and the digits of pi,
+                derived here from their definitions; pinned by the library
+                hashes above and by mpmath
 """
 from __future__ import annotations
 
@@ -35,7 +45,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "hf_oracle.c")
+_SRCS = [os.path.join(_HERE, "hf_oracle.c"), os.path.join(_HERE, "hf_oracle_hash.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -48,12 +58,12 @@ def build(force: bool = False) -> str:
     contraction of multiply-adds so that the double arithmetic is the one
     written in the source)."""
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + ".tmp%d" % os.getpid()
     subprocess.check_call([
         "gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-        "-o", tmp, _SRC, "-lm"])
+        "-o", tmp] + _SRCS + ["-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -83,6 +93,15 @@ def lib():
             "or_adam_step": (None, [P, P, P, P, i32, i32, f64, f64, f64, f64]),
             "or_blocks_per_sm": (i32, [i32] * 6),
             "or_register_bound": (i32, [i32] * 8),
+            "or_sha256_compress": (None, [P, P, P]),
+            "or_sha256": (None, [P, u64, P, P, P]),
+            "or_sha256d_scan": (None, [P, ctypes.c_uint32, i64, P, P, P]),
+            "or_blake256_compress": (None, [P, P, u64, P]),
+            "or_blake256": (None, [P, u64, P, P, P]),
+            "or_blake256_scan": (None, [P, ctypes.c_uint32, i64, P, P, P]),
+            "or_blake2s": (None, [P, u64, i32, P, P]),
+            "or_blake2b": (None, [P, u64, i32, P, P]),
+            "or_blake2b_scan": (None, [P, ctypes.c_uint32, i64, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -255,3 +274,137 @@ def speedup(t_base: float, t_fused: float):
     """The two readings of 'X% faster': (ratio T_base/T_fused, saving
     (T_base - T_fused)/T_base)."""
     return t_base / t_fused, (t_base - t_fused) / t_base
+
+
+# ---------------------------------------------------------------- hashes
+# Constants of the hash functions, derived from their definitions with exact
+# integer arithmetic.
+def _primes(n: int):
+    ps = []
+    k = 2
+    while len(ps) < n:
+        if all(k % p for p in ps if p * p <= k):
+            ps.append(k)
+        k += 1
+    return ps
+
+
+def _iroot(x: int, k: int) -> int:
+    """floor(x ** (1/k)) of a non-negative integer, by bisection."""
+    lo, hi = 0, 1 << (x.bit_length() // k + 1)
+    while lo < hi:
+        mid = (lo + hi + 1) // 2
+        if mid ** k <= x:
+            lo = mid
+        else:
+            hi = mid - 1
+    return lo
+
+
+def sha256_constants():
+    """(K, H0) of FIPS 180-4: K_t = the first 32 bits of the fractional part
+    of the cube root of the t-th prime (t < 64, Sec. 4.2.2); H0_i = the first
+    32 bits of the fractional part of the square root of the i-th prime
+    (i < 8, Sec. 5.3.3)."""
+    ps = _primes(64)
+    K = np.array([_iroot(p << 96, 3) & 0xFFFFFFFF for p in ps], np.uint32)
+    H0 = np.array([_iroot(p << 64, 2) & 0xFFFFFFFF for p in ps[:8]], np.uint32)
+    return K, H0
+
+
+def blake2b_iv():
+    """BLAKE2b's IV (RFC 7693 Sec. 2.6): the first 64 bits of the fractional
+    parts of the square roots of the first eight primes."""
+    return np.array([_iroot(p << 128, 2) & 0xFFFFFFFFFFFFFFFF for p in _primes(8)], np.uint64)
+
+
+def pi_words(nwords: int = 16):
+    """The first 32*nwords bits of the fractional part of pi as big-endian
+    32-bit words (BLAKE-256's constants), from Machin's formula
+    pi = 16 atan(1/5) - 4 atan(1/239) in fixed point with 64 guard bits."""
+    bits = 32 * nwords + 64
+    one = 1 << bits
+
+    def atan_inv(x):
+        total, term, k = 0, one // x, 0
+        while term:
+            total += term // (2 * k + 1) if k % 2 == 0 else -(term // (2 * k + 1))
+            term //= x * x
+            k += 1
+        return total
+
+    frac = (16 * atan_inv(5) - 4 * atan_inv(239) - 3 * one) >> 64
+    return np.array([(frac >> (32 * (nwords - 1 - i))) & 0xFFFFFFFF for i in range(nwords)],
+                    np.uint32)
+
+
+_HASH_CONST = {}
+
+
+def _hc():
+    if not _HASH_CONST:
+        K, H0 = sha256_constants()
+        _HASH_CONST.update(K=K, H0=H0, U=pi_words(16), B2B=blake2b_iv())
+    return _HASH_CONST
+
+
+def _bytes(msg) -> np.ndarray:
+    a = np.frombuffer(bytes(msg), np.uint8).copy()
+    return a if a.size else np.zeros(1, np.uint8)
+
+
+def sha256(msg) -> bytes:
+    c, m, out = _hc(), _bytes(msg), np.zeros(32, np.uint8)
+    lib().or_sha256(_p(m), len(bytes(msg)), _p(c["K"]), _p(c["H0"]), _p(out))
+    return out.tobytes()
+
+
+def blake256(msg) -> bytes:
+    c, m, out = _hc(), _bytes(msg), np.zeros(32, np.uint8)
+    lib().or_blake256(_p(m), len(bytes(msg)), _p(c["H0"]), _p(c["U"]), _p(out))
+    return out.tobytes()
+
+
+def blake2s(msg, nn: int = 32) -> bytes:
+    c, m, out = _hc(), _bytes(msg), np.zeros(nn, np.uint8)
+    lib().or_blake2s(_p(m), len(bytes(msg)), nn, _p(c["H0"]), _p(out))
+    return out.tobytes()
+
+
+def blake2b(msg, nn: int = 32) -> bytes:
+    c, m, out = _hc(), _bytes(msg), np.zeros(nn, np.uint8)
+    lib().or_blake2b(_p(m), len(bytes(msg)), nn, _p(c["B2B"]), _p(out))
+    return out.tobytes()
+
+
+def _header(header) -> np.ndarray:
+    h = np.frombuffer(bytes(header), np.uint8).copy()
+    assert h.size == 80
+    return h
+
+
+def sha256d_scan(header, first: int, n: int) -> np.ndarray:
+    """[n, 32] digests SHA-256(SHA-256(header)) with the nonce first + i as a
+    little-endian uint32 in bytes 76..79 of the 80-byte header."""
+    c, h, out = _hc(), _header(header), np.zeros((max(n, 1), 32), np.uint8)
+    lib().or_sha256d_scan(_p(h), first, n, _p(c["K"]), _p(c["H0"]), _p(out))
+    return out[:n]
+
+
+def blake256_scan(header, first: int, n: int) -> np.ndarray:
+    c, h, out = _hc(), _header(header), np.zeros((max(n, 1), 32), np.uint8)
+    lib().or_blake256_scan(_p(h), first, n, _p(c["H0"]), _p(c["U"]), _p(out))
+    return out[:n]
+
+
+def blake2b_scan(header, first: int, n: int) -> np.ndarray:
+    c, h, out = _hc(), _header(header), np.zeros((max(n, 1), 32), np.uint8)
+    lib().or_blake2b_scan(_p(h), first, n, _p(c["B2B"]), _p(out))
+    return out[:n]
+
+
+def hash_hits(digests: np.ndarray, first: int, target: int) -> np.ndarray:
+    """Sorted nonces whose digest bytes 28..31, read as a little-endian
+    uint32, are at most target: the scan's acceptance test."""
+    w = digests[:, 28:32].copy().view("<u4").reshape(-1)
+    return (np.nonzero(w <= np.uint32(target))[0].astype(np.uint64) + first).astype(np.uint32)

@@ -30,6 +30,10 @@ WORKLOADS = {
     "nway8": dict(bn=(64, 256, 56, 56), im2col=(32, 64, 56, 56), pool=(32, 128, 112, 112),
                   up=(32, 64, 128, 128), hist_n=1 << 26, philox_n=1 << 24,
                   poly_n=1 << 22, bf16_n=1 << 27),
+    # the three compute-bound hash scans over one random 80-byte header:
+    # nonces 0 .. n-1 each, sized so that each alone takes about the same
+    # time; target 2^16 accepts about one nonce in 65536.
+    "hash_pairs": dict(sha256d_n=1 << 24, blake256_n=1 << 24, blake2b_n=1 << 24, target=1 << 16),
 }
 
 POLY_ITERS = 64
@@ -94,6 +98,12 @@ def hist_input(n: int, seed: int = SEED):
 
 def bf16_inputs(n: int, seed: int = SEED):
     return bf16_uniform(n, seed + 6), bf16_uniform(n, seed + 7)
+
+
+def hash_header(seed: int = SEED) -> bytes:
+    """An 80-byte block header of uniform random bytes; the scans overwrite
+    its bytes 76..79 with each item's nonce."""
+    return bytes(bytes_u8(80, seed + 9).numpy().tobytes())
 
 
 def template_input(n: int, seed: int = SEED):
