@@ -407,4 +407,5 @@ def hash_hits(digests: np.ndarray, first: int, target: int) -> np.ndarray:
     """Sorted nonces whose digest bytes 28..31, read as a little-endian
     uint32, are at most target: the scan's acceptance test."""
     w = digests[:, 28:32].copy().view("<u4").reshape(-1)
-    return (np.nonzero(w <= np.uint32(target))[0].astype(np.uint64) + first).astype(np.uint32)
+    idx = np.nonzero(w <= np.uint32(target))[0].astype(np.uint64)
+    return np.sort(((idx + np.uint64(first)) & np.uint64(0xFFFFFFFF)).astype(np.uint32))

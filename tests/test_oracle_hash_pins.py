@@ -111,3 +111,7 @@ def test_hash_hits_brute_force():
     want = [1000 + i for i in range(500) if int.from_bytes(d[i, 28:32].tobytes(), "little") <= target]
     assert got.tolist() == want
     assert oracle.hash_hits(d, 0, 0xFFFFFFFF).size == 500
+    # nonces wrap modulo 2^32 and the set comes back sorted after the wrap
+    got = oracle.hash_hits(d, 0xFFFFFF00, target)
+    assert got.tolist() == sorted((0xFFFFFF00 + i) % (1 << 32) for i in range(500)
+                                  if int.from_bytes(d[i, 28:32].tobytes(), "little") <= target)
