@@ -68,7 +68,10 @@ typedef enum {
     HF_BODY_POLY = 6,         /* repeated degree-32 Horner chain                     */
     HF_BODY_BF16_AXPY = 7,    /* out = bf16(alpha*x + y)                             */
     HF_BODY_STREAM_TMPL = 8,  /* parametric stream kernel (cost-model corpus)        */
-    HF_BODY_COUNT = 9
+    HF_BODY_SHA256D = 9,      /* double SHA-256 nonce scan (Sec. 4.1 "SHA256")       */
+    HF_BODY_BLAKE256 = 10,    /* BLAKE-256, 14 rounds, nonce scan ("Blake256")       */
+    HF_BODY_BLAKE2B = 11,     /* BLAKE2b-256 nonce scan ("Blake2B")                  */
+    HF_BODY_COUNT = 12
 } hf_body_id;
 
 /* ------------------------------------------------------------------ */
@@ -164,6 +167,33 @@ typedef struct {
     int smem_bytes;
     float a, b;
 } hf_stream_tmpl_args;
+
+/* Nonce scan of an 80-byte block header, the work of the compute-bound hash
+ * kernels of Sec. 4.1 (a miner hashes one header again and again with a
+ * different nonce).  Item i (0 <= i < n) hashes `header` with bytes 76..79
+ * replaced by the nonce (first + i) mod 2^32 as a little-endian uint32:
+ *   HF_BODY_SHA256D   SHA-256(SHA-256(header))          (FIPS 180-4)
+ *   HF_BODY_BLAKE256  BLAKE-256, 14 rounds, salt 0      (the SHA-3 finalist)
+ *   HF_BODY_BLAKE2B   unkeyed BLAKE2b, 32-byte digest   (RFC 7693)
+ * each giving a 32-byte digest in the function's own byte order.
+ * digests: NULL, or [n][32] bytes (16-byte aligned) that receive every
+ * digest.  An item hits when digest bytes 28..31, read as a little-endian
+ * uint32, are <= target; each hit increments *hit_count (if hit_count is
+ * not NULL) and, while the old count is below hit_cap, stores its nonce at
+ * hits[old count] -- so the stored hits are in no particular order, and
+ * *hit_count ends as the total number of hits even past hit_cap.  The
+ * caller zeroes *hit_count.  HF_ERR_INVALID: n < 0 or n > 2^32, unaligned
+ * digests, hit_cap < 0, or hit_cap > 0 without hits and hit_count. */
+typedef struct {
+    uint8_t header[80];
+    uint32_t first;
+    uint32_t target;
+    int64_t n;
+    uint8_t *digests;
+    uint32_t *hits;
+    uint32_t *hit_count;
+    int32_t hit_cap;
+} hf_hash_scan_args;
 
 /* ------------------------------------------------------------------ */
 /* Kernels and fused kernels.                                          */
@@ -388,7 +418,9 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
 /* Measured throughput of one execution pipe on the current device, for
  * the compute terms of the ideal-overlap bound: what = 0 FP32 fused
  * multiply-adds per second, 1 32-bit integer multiplies (high or low half)
- * per second, 2 shared-memory atomic adds per second (conflict-free).
+ * per second, 2 shared-memory atomic adds per second (conflict-free),
+ * 3 32-bit integer ALU operations per second in the add / XOR / rotate mix
+ * of the hash rounds.
  * Runs a few milliseconds of calibration kernels on `stream`. */
 hf_status hf_calibrate(int what, void *stream, double *ops_per_s);
 

@@ -5,8 +5,9 @@
 // divided by that pipe's throughput.  These kernels measure the throughputs
 // on the running device (clock behaviour included) instead of using nominal
 // figures: independent FP32 fused multiply-add chains, 32-bit integer
-// multiplies (high and low halves, the Philox mix), and conflict-free
-// shared-memory atomic adds (the histogram's counting operation).
+// multiplies (high and low halves, the Philox mix), conflict-free
+// shared-memory atomic adds (the histogram's counting operation), and the
+// 32-bit add / XOR / rotate mix of the hash rounds.
 #include <algorithm>
 #include <vector>
 
@@ -46,6 +47,22 @@ __global__ void k_cal_imul(unsigned *out, int iters)
     for (int i = 0; i < iters; ++i)
 #pragma unroll
         for (int j = 0; j < kChains; ++j) c[j] = __umulhi(0xD2511F53u, c[j]) ^ (0xCD9E8D57u * c[j]);
+    unsigned s = 0;
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) s ^= c[j];
+    if (s == 0x12345678u) out[threadIdx.x] = s;
+}
+
+// One add, one XOR and one rotate (funnel shift) per step: the operation mix
+// of a BLAKE G function or a SHA-256 round.
+__global__ void k_cal_ialu(unsigned *out, int iters)
+{
+    unsigned c[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) c[j] = threadIdx.x * 2654435761u + j;
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int j = 0; j < kChains; ++j) c[j] = __funnelshift_r(c[j], c[j], 7) ^ (c[j] + 0x9E3779B9u);
     unsigned s = 0;
 #pragma unroll
     for (int j = 0; j < kChains; ++j) s ^= c[j];
@@ -93,7 +110,7 @@ hf_status time_ms(F f, cudaStream_t s, float *ms)
 
 extern "C" hf_status hf_calibrate(int what, void *stream, double *ops_per_s)
 {
-    if (!ops_per_s || what < 0 || what > 2) return hf::set_last_error(HF_ERR_INVALID, "bad calibration id");
+    if (!ops_per_s || what < 0 || what > 3) return hf::set_last_error(HF_ERR_INVALID, "bad calibration id");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -111,6 +128,9 @@ extern "C" hf_status hf_calibrate(int what, void *stream, double *ops_per_s)
     } else if (what == 1) {
         st = time_ms([&] { k_cal_imul<<<blocks, threads, 0, s>>>((unsigned *)out, iters); }, s, &ms);
         *ops_per_s = 2.0 * blocks * threads * iters * kChains / (ms * 1e-3);
+    } else if (what == 3) {
+        st = time_ms([&] { k_cal_ialu<<<blocks, threads, 0, s>>>((unsigned *)out, iters); }, s, &ms);
+        *ops_per_s = 3.0 * blocks * threads * iters * kChains / (ms * 1e-3);
     } else {
         st = time_ms([&] { k_cal_satom<<<blocks, threads, 8 * threads * 4, s>>>((unsigned *)out, iters / 4); },
                      s, &ms);

@@ -28,7 +28,8 @@ SingleEntry make_single()
 static const SingleEntry kSingles[] = {
     make_single<BodyBn>(),   make_single<BodyUpsample>(), make_single<BodyMaxpool>(),
     make_single<BodyIm2col>(), make_single<BodyHist>(),   make_single<BodyPhilox>(),
-    make_single<BodyPoly>(), make_single<BodyBf16Axpy>(), make_single<BodyStreamTmpl>()};
+    make_single<BodyPoly>(), make_single<BodyBf16Axpy>(), make_single<BodyStreamTmpl>(),
+    make_single<BodySha256d>(), make_single<BodyBlake256>(), make_single<BodyBlake2b>()};
 
 const SingleEntry *single_table(int *n)
 {

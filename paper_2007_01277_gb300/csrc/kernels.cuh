@@ -17,6 +17,7 @@
 
 #include "body_bn.cuh"
 #include "body_fp.cuh"
+#include "body_hash.cuh"
 #include "body_int.cuh"
 #include "body_resample.cuh"
 
@@ -109,10 +110,10 @@ struct NwayParams {
     int n_int;                                  // intervals
     int warp_begin[HF_MAX_INTERVALS + 1];       // interval i = warps [wb[i], wb[i+1])
     unsigned smem_off[HF_MAX_INTERVALS];        // shared slice of interval i
-    int n_sched;                                // kernels
-    int sched_body[HF_MAX_SCHEDULE];            // body id of kernel j
-    int sched_int[HF_MAX_SCHEDULE];             // interval of kernel j
-    unsigned args_off[HF_MAX_SCHEDULE];         // argument block of kernel j in blob
+    int int_first[HF_MAX_INTERVALS + 1];        // interval i runs slots [if[i], if[i+1])
+    int sched_body[HF_MAX_SCHEDULE];            // body id of slot j (slots sorted by interval)
+    unsigned args_off[HF_MAX_SCHEDULE];         // argument block of slot j in blob
+    unsigned char warp_int[32];                 // interval of each warp of the block
     unsigned long long *trace;                  // optional: [n_int][2] first start / last end (ns)
     alignas(16) unsigned char blob[kNwayBlob];
 };
@@ -148,16 +149,26 @@ __device__ __forceinline__ void dispatch(int body, const unsigned char *args, co
     case HF_BODY_STREAM_TMPL:
         BodyStreamTmpl::run(*reinterpret_cast<const BodyStreamTmpl::Args *>(args), c);
         break;
+    case HF_BODY_SHA256D:
+        BodySha256d::run(*reinterpret_cast<const BodySha256d::Args *>(args), c);
+        break;
+    case HF_BODY_BLAKE256:
+        BodyBlake256::run(*reinterpret_cast<const BodyBlake256::Args *>(args), c);
+        break;
+    case HF_BODY_BLAKE2B:
+        BodyBlake2b::run(*reinterpret_cast<const BodyBlake2b::Args *>(args), c);
+        break;
     default: break;
     }
 }
 
-__device__ __forceinline__ void nway_body(const NwayParams &p)
+// The interval context of interval i, rebuilt from the parameter bank and
+// special registers each time it is needed, so nothing of it stays live in
+// registers across a body (register pressure under a cap is what decides
+// whether the fused kernel spills).
+__device__ __forceinline__ Ctx interval_ctx(const NwayParams &p, int i)
 {
     extern __shared__ __align__(128) unsigned char hf_smem[];
-    const int warp = threadIdx.x >> 5;
-    int i = 0;
-    while (i + 1 < p.n_int && warp >= p.warp_begin[i + 1]) ++i;
     Ctx c;
     c.tid = threadIdx.x - 32 * p.warp_begin[i];
     c.nthreads = 32 * (p.warp_begin[i + 1] - p.warp_begin[i]);
@@ -165,24 +176,25 @@ __device__ __forceinline__ void nway_body(const NwayParams &p)
     c.block = blockIdx.x;
     c.grid = gridDim.x;
     c.smem = hf_smem + p.smem_off[i];
-    {
-        const unsigned end = dynamic_smem_end(hf_smem);
-        c.smem_end = i + 1 < p.n_int
-                         ? min(end, (unsigned)__cvta_generic_to_shared(hf_smem) + p.smem_off[i + 1])
-                         : end;
-    }
-    const bool lead = p.trace && (threadIdx.x & 31) == 0;
-    if (lead) atomicMin(p.trace + 2 * i, global_ns());
-    bool first = true;
-    for (int j = 0; j < p.n_sched; ++j) {
-        if (p.sched_int[j] != i) continue;
+    const unsigned end = dynamic_smem_end(hf_smem);
+    c.smem_end = i + 1 < p.n_int
+                     ? min(end, (unsigned)__cvta_generic_to_shared(hf_smem) + p.smem_off[i + 1])
+                     : end;
+    return c;
+}
+
+__device__ __forceinline__ void nway_body(const NwayParams &p)
+{
+    const int i = p.warp_int[threadIdx.x >> 5];
+    if (p.trace && (threadIdx.x & 31) == 0) atomicMin(p.trace + 2 * i, global_ns());
+    const int j0 = p.int_first[i];
+    for (int j = j0; j < p.int_first[i + 1]; ++j) {
         // kernels sharing an interval share its shared slice: the previous
         // one must be done with it before the next starts
-        if (!first) interval_sync(c);
-        first = false;
-        dispatch(p.sched_body[j], p.blob + p.args_off[j], c);
+        if (j > j0) interval_sync(interval_ctx(p, i));
+        dispatch(p.sched_body[j], p.blob + p.args_off[j], interval_ctx(p, i));
     }
-    if (lead) atomicMax(p.trace + 2 * i + 1, global_ns());
+    if (p.trace && (threadIdx.x & 31) == 0) atomicMax(p.trace + 2 * i + 1, global_ns());
 }
 
 __global__ void __launch_bounds__(512) k_nway(const __grid_constant__ NwayParams p);
@@ -245,6 +257,7 @@ const Instance *pair_table_0(int *n);
 const Instance *pair_table_1(int *n);
 const Instance *pair_table_2(int *n);
 const Instance *pair_table_3(int *n);
+const Instance *pair_table_4(int *n);
 const Instance *nway_table(int *n);
 
 // Standalone kernels: one per body, no register bound.

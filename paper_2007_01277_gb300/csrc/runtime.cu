@@ -64,7 +64,8 @@ const BodyOps &body_ops(int id)
         ops<BodyMaxpool>("maxpool3s2"), ops<BodyIm2col>("im2col3"),
         ops<BodyHist>("hist256"),    ops<BodyPhilox>("philox"),
         ops<BodyPoly>("poly"),       ops<BodyBf16Axpy>("bf16_axpy"),
-        ops<BodyStreamTmpl>("stream_tmpl")};
+        ops<BodyStreamTmpl>("stream_tmpl"), ops<BodySha256d>("sha256d"),
+        ops<BodyBlake256>("blake256"), ops<BodyBlake2b>("blake2b")};
     return kOps[id];
 }
 
@@ -84,7 +85,8 @@ const Registry &registry()
     static Registry r;
     static std::once_flag once;
     std::call_once(once, [] {
-        const Instance *(*tabs[])(int *) = {pair_table_0, pair_table_1, pair_table_2, pair_table_3};
+        const Instance *(*tabs[])(int *) = {pair_table_0, pair_table_1, pair_table_2, pair_table_3,
+                                                   pair_table_4};
         for (auto t : tabs) {
             int n = 0;
             const Instance *p = t(&n);
@@ -308,18 +310,28 @@ hf_status nway_params(const hf_fused_t *f, const void *const *args, NwayParams *
         off += align128(need);
     }
     p->warp_begin[f->n_int] = w;
-    p->n_sched = f->n;
+    for (int i = 0; i < f->n_int; ++i)
+        for (int k = p->warp_begin[i]; k < p->warp_begin[i + 1]; ++k) p->warp_int[k] = (unsigned char)i;
+    // slots sorted by interval; kernels sharing an interval keep the
+    // caller's order
     size_t boff = 0;
-    for (int j = 0; j < f->n; ++j) {
-        const size_t sz = body_ops(f->sched_body[j]).args_size;
-        boff = (boff + 15) / 16 * 16;
-        if (boff + sz > (size_t)kNwayBlob) return fail(HF_ERR_INVALID, "argument blocks exceed %d B", kNwayBlob);
-        std::memcpy(p->blob + boff, args[j], sz);
-        p->sched_body[j] = f->sched_body[j];
-        p->sched_int[j] = f->sched_int[j];
-        p->args_off[j] = (unsigned)boff;
-        boff += sz;
+    int slot = 0;
+    for (int i = 0; i < f->n_int; ++i) {
+        p->int_first[i] = slot;
+        for (int j = 0; j < f->n; ++j) {
+            if (f->sched_int[j] != i) continue;
+            const size_t sz = body_ops(f->sched_body[j]).args_size;
+            boff = (boff + 15) / 16 * 16;
+            if (boff + sz > (size_t)kNwayBlob)
+                return fail(HF_ERR_INVALID, "argument blocks exceed %d B", kNwayBlob);
+            std::memcpy(p->blob + boff, args[j], sz);
+            p->sched_body[slot] = f->sched_body[j];
+            p->args_off[slot] = (unsigned)boff;
+            boff += sz;
+            ++slot;
+        }
     }
+    p->int_first[f->n_int] = slot;
     *smem = (unsigned)off;
     return HF_OK;
 }

@@ -20,9 +20,11 @@ STATUS = {0: "HF_OK", -1: "HF_ERR_INVALID", -2: "HF_ERR_SPLIT", -3: "HF_ERR_BARR
           -4: "HF_ERR_SMEM", -5: "HF_ERR_REGS", -6: "HF_ERR_UNSUPPORTED", -7: "HF_ERR_CUDA",
           -8: "HF_ERR_TIMEOUT"}
 
-BN_STATS, UPSAMPLE2X, MAXPOOL3S2, IM2COL3, HIST256, PHILOX, POLY, BF16_AXPY, STREAM_TMPL = range(9)
+(BN_STATS, UPSAMPLE2X, MAXPOOL3S2, IM2COL3, HIST256, PHILOX, POLY, BF16_AXPY, STREAM_TMPL,
+ SHA256D, BLAKE256, BLAKE2B) = range(12)
 BODY_NAMES = ["bn_stats", "upsample2x", "maxpool3s2", "im2col3", "hist256", "philox", "poly",
-              "bf16_axpy", "stream_tmpl"]
+              "bf16_axpy", "stream_tmpl", "sha256d", "blake256", "blake2b"]
+HASH_BODIES = (SHA256D, BLAKE256, BLAKE2B)
 MAX_INTERVALS = 15
 MAX_SCHEDULE = 16
 
@@ -68,8 +70,14 @@ class StreamTmplArgs(ctypes.Structure):
                 ("smem_bytes", _i32), ("a", _f32), ("b", _f32)]
 
 
+class HashScanArgs(ctypes.Structure):
+    _fields_ = [("header", ctypes.c_uint8 * 80), ("first", ctypes.c_uint32),
+                ("target", ctypes.c_uint32), ("n", _i64), ("digests", _P), ("hits", _P),
+                ("hit_count", _P), ("hit_cap", _i32)]
+
+
 ARGS_TYPES = [BnStatsArgs, Upsample2xArgs, Maxpool3s2Args, Im2col3Args, Hist256Args, PhiloxArgs,
-              PolyArgs, Bf16AxpyArgs, StreamTmplArgs]
+              PolyArgs, Bf16AxpyArgs, StreamTmplArgs, HashScanArgs, HashScanArgs, HashScanArgs]
 
 
 class KernelDesc(ctypes.Structure):
@@ -349,6 +357,20 @@ def stream_tmpl_args(x, y, k, n_barriers=0, smem_bytes=0, a=0.999, b=0.001):
     return _keep(StreamTmplArgs(_ptr(x), _ptr(y), x.numel(), k, n_barriers, smem_bytes, a, b), x, y)
 
 
+def hash_scan_args(header, n, first=0, target=0, digests=None, hits=None, hit_count=None):
+    """Argument block of the three hash scans (same layout for each).
+    header: 80 bytes; digests: None or a uint8 tensor of n*32 bytes; hits:
+    None or an int32 tensor (its length is the capacity); hit_count: None or
+    a zeroed int32 tensor of one element."""
+    h = bytes(header)
+    if len(h) != 80:
+        raise ValueError("the header is 80 bytes")
+    a = HashScanArgs((ctypes.c_uint8 * 80)(*h), first & 0xFFFFFFFF, target & 0xFFFFFFFF, n,
+                     _ptr(digests), _ptr(hits), _ptr(hit_count),
+                     0 if hits is None else hits.numel())
+    return _keep(a, digests, hits, hit_count)
+
+
 # ----------------------------------------------------------------- profiling search
 def hf_time_fused(f, args, grid=0, reps=10, flush_l2=True, stream=None):
     m, lo, hi = _f32(), _f32(), _f32()
@@ -408,7 +430,7 @@ def hf_autotune_nway(kernels, args, max_evals=200, reps=5, flush_l2=False, strea
     return d, list(single)
 
 
-CAL_FFMA, CAL_IMUL, CAL_SMEM_ATOMIC = 0, 1, 2
+CAL_FFMA, CAL_IMUL, CAL_SMEM_ATOMIC, CAL_IALU = 0, 1, 2, 3
 
 
 def hf_calibrate(what, stream=None):

@@ -98,6 +98,10 @@ def test_calibration_in_plausible_range():
     assert 0.2 * nominal < ffma < 1.1 * nominal
     assert H.hf_calibrate(H.CAL_IMUL) > 0
     assert H.hf_calibrate(H.CAL_SMEM_ATOMIC) > 0
+    # at most 128 integer ALU lanes per SM per clock
+    assert 0.05 * nominal < H.hf_calibrate(H.CAL_IALU) < 1.1 * nominal
+    with pytest.raises(H.HFError):
+        H.hf_calibrate(4)
 
 
 def test_stream_wait_times_out_on_long_kernel():
