@@ -25,6 +25,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2007_01277_gb300 import workloads as _W  # noqa: E402  (seeded input recipes)
+
 METRIC = ("fused vs serial/2-stream time (µs), % of ideal-overlap roofline, model regret")
 UP_SHAPE = (32, 64, 128, 128)
 POOL_SHAPE = (32, 128, 112, 112)
@@ -158,6 +160,21 @@ PAIR_SPECS = {
                     desc="bn stats FP32 8x64x32x32 ~N(0,1) + 64x degree-32 Horner on 2^20 FP32 "
                          "~U(-1,1), fused in one launch"),
 }
+# the compute+compute pairs of the three hash scans (Sec. 4.2's negative
+# case): each scan over one random 80-byte header, sized to ~2 ms alone
+_HP = _W.WORKLOADS["hash_pairs"]
+HASH_N = {h: _HP[h + "_n"] for h in ("sha256d", "blake256", "blake2b")}
+# 32-bit integer operations per hash as the definitions state them (a
+# three-input add or XOR counts once, a rotate once, a 64-bit operation
+# twice): SHA-256 compression 64 x 14 + 48 x 10 = 1376, two per nonce;
+# BLAKE-256 14 rounds x 8 G x 14; BLAKE2b 12 rounds x 8 G x 22
+HASH_OPS = {"sha256d": 2 * 1376, "blake256": 14 * 8 * 14, "blake2b": 12 * 8 * 22}
+for _a, _b in (("sha256d", "blake256"), ("sha256d", "blake2b"), ("blake256", "blake2b")):
+    PAIR_SPECS[_a + "_" + _b] = dict(
+        d0=512, splits=tuple(range(64, 512, 64)), caps=(0, 48, 64, 96), bps=(1, 2, 3, 4), flush=True,
+        name="fused_%s_%s" % (_a, _b), hashes=(_a, _b),
+        desc="%s nonce scan (%d nonces) + %s nonce scan (%d nonces) of a random 80-byte header, "
+             "fused in one launch" % (_a, HASH_N[_a], _b, HASH_N[_b]))
 
 
 def make_pair(name, H, W, dev):
@@ -192,12 +209,25 @@ def make_pair(name, H, W, dev):
         return ((H.BN_STATS, H.POLY), [H.bn_stats_args(xb, m, v, ws),
                                        H.poly_args(xq, yq, W.poly_coefficients().tolist())],
                 nbytes, ops, [(xb_h, xb), (xq_h, xq)], [m, v, yq, ws])
+    if name in PAIR_SPECS and "hashes" in PAIR_SPECS[name]:
+        ids = {"sha256d": H.SHA256D, "blake256": H.BLAKE256, "blake2b": H.BLAKE2B}
+        args, outs = [], []
+        for k, hname in enumerate(PAIR_SPECS[name]["hashes"]):
+            cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+            hits = torch.zeros(1 << 12, dtype=torch.int32, device=dev)
+            args.append(H.hash_scan_args(W.hash_header(k), HASH_N[hname], 0,
+                                         W.WORKLOADS["hash_pairs"]["target"], None, hits, cnt))
+            outs += [cnt, hits]
+        hs = PAIR_SPECS[name]["hashes"]
+        ops = {"ialu": sum(HASH_N[h] * HASH_OPS[h] for h in hs)}
+        return (tuple(ids[h] for h in hs), args, 0, ops, [], outs)
     raise SystemExit("unknown pair workload " + name)
 
 
 def pipe_peaks(H, stream):
     return {"ffma": H.hf_calibrate(H.CAL_FFMA, stream), "imul": H.hf_calibrate(H.CAL_IMUL, stream),
-            "smem_atomic": H.hf_calibrate(H.CAL_SMEM_ATOMIC, stream)}
+            "smem_atomic": H.hf_calibrate(H.CAL_SMEM_ATOMIC, stream),
+            "ialu": H.hf_calibrate(H.CAL_IALU, stream)}
 
 
 def ideal_us(nbytes, ops, peaks, hbm_gbs):
@@ -353,18 +383,30 @@ def run_pair(cx, name):
 
     t_e2e = statistics.median(cx.timed(step_e2e, max(3, K // 20), warm=1))
     h2d = sum(d.numel() * d.element_size() for _, d in host_in)
+    if "hashes" in spec:
+        h2d += 80 * len(args)   # the headers travel in the launch's parameter block
     d2h = sum(o.numel() * o.element_size() for o in outs)
 
     hbm, peak_kind = measured_peaks()
     peaks = pipe_peaks(H, st)
     t_ideal, terms = ideal_us(nbytes, ops, peaks, hbm)
-    achieved = nbytes / (t_fused * 1e-6) / 1e9
+    if "hashes" in spec:
+        achieved = ops["ialu"] / (t_fused * 1e-6) / 1e12
+        roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peaks["ialu"] / 1e12, 3),
+                    "unit": "Tops/s", "frac": round(achieved * 1e12 / peaks["ialu"], 4),
+                    "traffic": load_traffic(spec["name"]),
+                    "peak_source": "measured in this run: 32-bit add/XOR/rotate mix (calibration kernel)"}
+    else:
+        achieved = nbytes / (t_fused * 1e-6) / 1e9
+        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(achieved / hbm, 4), "traffic": load_traffic(spec["name"]),
+                    "peak_source": peak_kind}
     info = H.hf_query(fused, args)
     return {
         "metric": METRIC, "value": round(t_fused, 3), "unit": "us",
         "n_gpus": cx.world, "steps": K, "warmup": Wm, "ms_per_step": round(t_fused / 1e3, 6),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if name != "hist_philox" else "u8/u32", "data": "synthetic (seeded torch.Generator, CPU-drawn)",
+        "dtype": {"hist_philox": "u8/u32"}.get(name, "u32/u64" if "hashes" in spec else "f32"), "data": "synthetic (seeded torch.Generator, CPU-drawn)",
         "config": {"workload": spec["desc"], "split": best["split"], "d0": d0, "regcap": best["regcap"],
                    "grid": grid, "regs": info["regs"], "spill_bytes": info["spill_bytes"],
                    "l2": "L2 flushed (512 MB write) before every timed launch" if fl else
@@ -381,9 +423,7 @@ def run_pair(cx, name):
                    "naive_even_split_us": round(naive["time_us"], 3) if naive else None,
                    "vfuse_us": round(vfuse[0], 3) if vfuse else None,
                    "vfuse_block": vfuse[1] if vfuse else None},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4), "traffic": load_traffic(spec["name"]),
-                     "peak_source": peak_kind},
+        "roofline": roofline,
         "e2e": {"value": round(t_e2e, 2), "unit": "us", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": K,
         "clocks": clk.summary(),
@@ -678,6 +718,18 @@ def cpu_baseline_for(workload: str):
         t_q = _pool_time([lambda ch=ch: oracle.poly(ch, c) for ch in chunks], cores) * 64
         return {"value": round((t_b + t_q) * 1e6, 1), "unit": "us", "cores": cores, "kind": "oracle",
                 "sample": "bn on the whole input, poly on 2^14 of 2^20 elements (x64)"}
+    if workload in PAIR_SPECS and "hashes" in PAIR_SPECS[workload]:
+        scans = {"sha256d": oracle.sha256d_scan, "blake256": oracle.blake256_scan,
+                 "blake2b": oracle.blake2b_scan}
+        total, sample = 0.0, []
+        for k, h in enumerate(PAIR_SPECS[workload]["hashes"]):
+            per = (1 << 16) // cores
+            hdr = W.hash_header(k)
+            jobs = [lambda i=i, h=h, hdr=hdr: scans[h](hdr, i * per, per) for i in range(cores)]
+            total += _pool_time(jobs, cores) * HASH_N[h] / (per * cores)
+            sample.append("%s on %d of %d nonces" % (h, per * cores, HASH_N[h]))
+        return {"value": round(total * 1e6, 1), "unit": "us", "cores": cores, "kind": "oracle",
+                "sample": ", ".join(sample) + ", scaled"}
     if workload == "nway8":
         sp = W.WORKLOADS["nway8"]
         parts = []

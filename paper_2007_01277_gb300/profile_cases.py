@@ -14,6 +14,9 @@ and prints the median CUDA-event time per launch.  Cases:
   bn_large        bn stats 64x256x56x56
   im2col          im2col 32x64x56x56
   bf16            bf16 scale+add on 2^27
+  fused_sha256d_blake2b  SHA-256d scan of 2^24 nonces + BLAKE2b scan of
+                  21*2^20 nonces fused (hits only, target 2^16)
+  sha256d, blake256, blake2b  the hash scans alone (2^24, 2^25, 21*2^20)
   nway8           the eight kernels of the N-way workload in one launch with a
                   fixed plan (--plan "io;threads;cap", default the autotuned
                   4-interval plan)
@@ -77,6 +80,15 @@ def build(case, scale, dev):
         x, y = (t.to(dev) for t in W.bf16_inputs(n1(1 << 27)))
         o = torch.empty_like(x)
         out["bf16"] = (H.BF16_AXPY, H.bf16_axpy_args(x, y, o), (x, y, o))
+    hp = W.WORKLOADS["hash_pairs"]
+    for k, (hname, body) in enumerate((("sha256d", H.SHA256D), ("blake256", H.BLAKE256),
+                                       ("blake2b", H.BLAKE2B))):
+        if case == hname or (case.startswith("fused_") and hname in case.split("_")[1:]):
+            cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+            hits = torch.zeros(1 << 12, dtype=torch.int32, device=dev)
+            a = H.hash_scan_args(W.hash_header(k), n1(hp[hname + "_n"]), 0, hp["target"], None,
+                                 hits, cnt)
+            out[hname] = (body, a, (cnt, hits))
     if case == "nway8":
         sp = W.WORKLOADS["nway8"]
         xb = W.bn_input((nb(64),) + sp["bn"][1:]).to(dev)

@@ -33,7 +33,7 @@ WORKLOADS = {
     # the three compute-bound hash scans over one random 80-byte header:
     # nonces 0 .. n-1 each, sized so that each alone takes about the same
     # time; target 2^16 accepts about one nonce in 65536.
-    "hash_pairs": dict(sha256d_n=1 << 24, blake256_n=1 << 24, blake2b_n=1 << 24, target=1 << 16),
+    "hash_pairs": dict(sha256d_n=1 << 24, blake256_n=1 << 25, blake2b_n=21 << 20, target=1 << 16),
 }
 
 POLY_ITERS = 64

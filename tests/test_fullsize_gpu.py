@@ -120,3 +120,34 @@ def test_nway8_full_size_converged_plan():
     assert np.array_equal(bits16(o16[sl]), ref16)
     tail = slice(sp["bf16_n"] - 4096, sp["bf16_n"])
     assert np.array_equal(bits16(o16[tail]), oracle.bf16_axpy(bits16(x16[tail]), bits16(y16[tail]), 0.5))
+
+
+def test_hash_pair_full_size_bench_config():
+    """SHA-256d over 2^24 nonces + BLAKE2b over 21*2^20 nonces fused at
+    384/128 of 512 under a 64-register cap, 2 blocks/SM: sampled digests
+    against the oracle, every stored hit re-hashed by the oracle, and the hit
+    count equal to the number of digests that pass the test."""
+    hp = W.WORKLOADS["hash_pairs"]
+    specs = [(H.SHA256D, hp["sha256d_n"], oracle.sha256d_scan, W.hash_header(0)),
+             (H.BLAKE2B, hp["blake2b_n"], oracle.blake2b_scan, W.hash_header(1))]
+    bufs, args = [], []
+    for body, n, _, hdr in specs:
+        dig = torch.empty(n * 32, dtype=torch.uint8, device=DEV)
+        hits = torch.full((1 << 12,), -1, dtype=torch.int32, device=DEV)
+        cnt = torch.zeros(1, dtype=torch.int32, device=DEV)
+        bufs.append((dig, hits, cnt))
+        args.append(H.hash_scan_args(hdr, n, 0, hp["target"], dig, hits, cnt))
+    f = H.hf_fuse(H.hf_register_kernel(H.SHA256D), H.hf_register_kernel(H.BLAKE2B), 384, 512, 64)
+    H.hf_launch(f, args, grid(2))
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(3)
+    for (body, n, scan, hdr), (dig, hits, cnt) in zip(specs, bufs):
+        d = dig.cpu().numpy().reshape(n, 32)
+        for i in [0, n - 1] + list(rng.integers(0, n, 200)):
+            assert np.array_equal(d[i], scan(hdr, int(i), 1)[0]), (H.BODY_NAMES[body], i)
+        count = int(cnt.item())
+        assert count == oracle.hash_hits(d, 0, hp["target"]).size > 0
+        stored = hits.cpu().numpy().view(np.uint32)[: min(count, hits.numel())]
+        for nonce in stored:
+            ref = scan(hdr, int(nonce), 1)
+            assert oracle.hash_hits(ref, int(nonce), hp["target"]).tolist() == [nonce]
