@@ -415,6 +415,56 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
                            int reps, int flush_l2, void *stream, hf_nway_plan *best,
                            float *standalone_us);
 
+/* ------------------------------------------------------------------ */
+/* Source-level front-end: Algorithm 1 (Sec. 3.1) as a transformation of
+ * CUDA source text (the paper's automatic tool, Sec. 3.3), compiled at run
+ * time with NVRTC for the current device.  Kernels are 1-D: in each
+ * kernel's body threadIdx.x becomes the interval's thread index, blockDim.x
+ * its size, __syncthreads() "bar.sync id, d" (id 1 for kernel a, 2 for b),
+ * and "extern __shared__ T name[]" a pointer to the kernel's slice of the
+ * combined dynamic shared memory; blockIdx and gridDim are unchanged.
+ * HF_ERR_UNSUPPORTED: threadIdx/blockDim .y/.z, __syncthreads_count/and/or,
+ * kernel templates, these builtins in a __device__ helper, other forms of
+ * extern __shared__; HF_ERR_INVALID: no such kernel, or NVRTC rejected the
+ * source (hf_last_error() has the start of its log) or is not installed. */
+typedef struct hf_src_module_t *hf_src_module;
+
+/* The fused source: kernel name_a of src_a on threads [0, split), kernel
+ * name_b of src_b (NULL: the same source) on [split, d0), as one
+ * extern "C" __global__ kernel "hf_src_fused" whose parameters are a's, then
+ * b's, then the byte offset of b's dynamic shared memory.  Written to
+ * out[0..cap) NUL-terminated; *len = bytes needed including the NUL
+ * (out may be NULL to query it).  Two different sources are concatenated,
+ * so their file-scope names must not collide.  HF_ERR_SPLIT as hf_fuse. */
+hf_status hf_src_fuse(const char *src_a, const char *name_a, const char *src_b, const char *name_b,
+                      int split, int d0, char *out, size_t cap, size_t *len);
+
+/* Compile a source with NVRTC (no GPU needed) and check that it defines
+ * kernel `name`; the compiler log goes to log[0..cap) when log != NULL. */
+hf_status hf_src_compile_check(const char *src, const char *name, int regcap, char *log, size_t cap);
+
+/* Compile and load: one kernel of a source as it is (the standalone
+ * launch), or the fused kernel of two (regcap = register bound, 0 none). */
+hf_status hf_src_load(const char *src, const char *name, int regcap, hf_src_module *out);
+hf_status hf_src_fuse_load(const char *src_a, const char *name_a, const char *src_b, const char *name_b,
+                           int split, int d0, int regcap, hf_src_module *out);
+
+/* Launch a single kernel: params[i] points at the value of parameter i
+ * (the cuLaunchKernel convention); asynchronous on `stream`. */
+hf_status hf_src_launch(hf_src_module m, void **params, int grid, int block, size_t dyn_smem,
+                        void *stream);
+
+/* Launch a fused module on `grid` blocks of d0 threads: params_a / params_b
+ * as above for each kernel; each kernel gets its own dynamic shared memory
+ * of the given size (b's slice starts 128-byte aligned after a's). */
+hf_status hf_src_launch_fused(hf_src_module m, void **params_a, void **params_b, size_t dyn_smem_a,
+                              size_t dyn_smem_b, int grid, void *stream);
+
+/* Registers per thread, local (spill) bytes per thread, static shared
+ * memory and the largest block of the loaded kernel. */
+hf_status hf_src_query(hf_src_module m, int *regs, int *local_bytes, int *static_smem, int *max_threads);
+void hf_src_unload(hf_src_module m);
+
 /* Measured throughput of one execution pipe on the current device, for
  * the compute terms of the ideal-overlap bound: what = 0 FP32 fused
  * multiply-adds per second, 1 32-bit integer multiplies (high or low half)

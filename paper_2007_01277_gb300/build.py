@@ -71,7 +71,7 @@ def build(verbose: bool = False, jobs: int | None = None, force: bool = False) -
     if force or cmds or not os.path.exists(LIB):
         tmp = LIB + ".tmp%d" % os.getpid()
         run([nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs +
-            ["-Xlinker", "-rpath=" + cuda_lib_dir()])
+            ["-ldl", "-Xlinker", "-rpath=" + cuda_lib_dir()])
         os.replace(tmp, LIB)
     return LIB
 

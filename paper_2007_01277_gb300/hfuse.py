@@ -163,6 +163,19 @@ def _load():
         "hf_autotune_nway": (_i32, [ctypes.POINTER(_P), _i32, ctypes.POINTER(_P), _i32, _i32, _i32,
                                     _P, ctypes.POINTER(NwayPlan), ctypes.POINTER(_f32)]),
         "hf_calibrate": (_i32, [_i32, _P, ctypes.POINTER(ctypes.c_double)]),
+        "hf_src_fuse": (_i32, [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, _i32,
+                               _i32, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+        "hf_src_compile_check": (_i32, [ctypes.c_char_p, ctypes.c_char_p, _i32, ctypes.c_char_p,
+                                        ctypes.c_size_t]),
+        "hf_src_load": (_i32, [ctypes.c_char_p, ctypes.c_char_p, _i32, ctypes.POINTER(_P)]),
+        "hf_src_fuse_load": (_i32, [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p,
+                                    _i32, _i32, _i32, ctypes.POINTER(_P)]),
+        "hf_src_launch": (_i32, [_P, ctypes.POINTER(_P), _i32, _i32, ctypes.c_size_t, _P]),
+        "hf_src_launch_fused": (_i32, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_size_t,
+                                       ctypes.c_size_t, _i32, _P]),
+        "hf_src_query": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                ctypes.POINTER(_i32)]),
+        "hf_src_unload": (None, [_P]),
         "hf_tmpl_features": (_i32, [ctypes.POINTER(StreamTmplArgs), ctypes.POINTER(StreamTmplArgs),
                                     _i32, _i32, _i32, _i32, _i32, _i32, ctypes.c_double,
                                     ctypes.c_double, ctypes.POINTER(_f32)]),
@@ -494,3 +507,82 @@ def hf_launch_traced(f, args, grid=0, stream=None):
     torch.cuda.synchronize()
     h = tr.cpu().numpy().view("uint64")
     return [(int(h[2 * i]), int(h[2 * i + 1])) for i in range(n_int) if h[2 * i + 1] > 0]
+
+
+# ----------------------------------------------------------------- source front-end
+def _b(x):
+    return None if x is None else (x.encode() if isinstance(x, str) else bytes(x))
+
+
+def hf_src_fuse(src_a, name_a, src_b, name_b, split, d0):
+    """The generated CUDA source of the fused kernel (Algorithm 1 on source)."""
+    n = ctypes.c_size_t()
+    _check("hf_src_fuse", lib.hf_src_fuse(_b(src_a), _b(name_a), _b(src_b), _b(name_b), split, d0,
+                                          None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check("hf_src_fuse", lib.hf_src_fuse(_b(src_a), _b(name_a), _b(src_b), _b(name_b), split, d0,
+                                          buf, n.value, ctypes.byref(n)))
+    return buf.value.decode()
+
+
+def hf_src_compile_check(src, name, regcap=0):
+    """Compile with NVRTC (no GPU needed); returns the compiler log."""
+    log = ctypes.create_string_buffer(1 << 16)
+    _check("hf_src_compile_check", lib.hf_src_compile_check(_b(src), _b(name), regcap, log, len(log)))
+    return log.value.decode(errors="replace")
+
+
+def hf_src_load(src, name, regcap=0):
+    h = _P()
+    _check("hf_src_load", lib.hf_src_load(_b(src), _b(name), regcap, ctypes.byref(h)))
+    return h
+
+
+def hf_src_fuse_load(src_a, name_a, src_b, name_b, split, d0, regcap=0):
+    h = _P()
+    _check("hf_src_fuse_load", lib.hf_src_fuse_load(_b(src_a), _b(name_a), _b(src_b), _b(name_b), split,
+                                                    d0, regcap, ctypes.byref(h)))
+    return h
+
+
+class KernelParams:
+    """Parameter values of a source kernel in launch order: torch tensors
+    pass their device pointer, ctypes values pass as they are, Python ints
+    as C int and floats as C float.  Holds the values while it lives."""
+
+    def __init__(self, *values):
+        self.vals = []
+        for v in values:
+            if hasattr(v, "data_ptr"):
+                self.vals.append(ctypes.c_void_p(v.data_ptr()))
+            elif isinstance(v, ctypes._SimpleCData):
+                self.vals.append(v)
+            elif isinstance(v, bool) or not isinstance(v, (int, float)):
+                raise TypeError("unsupported parameter value %r" % (v,))
+            elif isinstance(v, int):
+                self.vals.append(ctypes.c_int(v))
+            else:
+                self.vals.append(ctypes.c_float(v))
+        self.keep = values
+        self.array = (_P * max(1, len(self.vals)))(
+            *[ctypes.cast(ctypes.pointer(v), _P) for v in self.vals])
+
+
+def hf_src_launch(m, params, grid, block, dyn_smem=0, stream=None):
+    _check("hf_src_launch", lib.hf_src_launch(m, params.array, grid, block, dyn_smem, _stream_ptr(stream)))
+
+
+def hf_src_launch_fused(m, params_a, params_b, grid, dyn_smem_a=0, dyn_smem_b=0, stream=None):
+    _check("hf_src_launch_fused", lib.hf_src_launch_fused(m, params_a.array, params_b.array, dyn_smem_a,
+                                                          dyn_smem_b, grid, _stream_ptr(stream)))
+
+
+def hf_src_query(m):
+    r, l, s_, t = _i32(), _i32(), _i32(), _i32()
+    _check("hf_src_query", lib.hf_src_query(m, ctypes.byref(r), ctypes.byref(l), ctypes.byref(s_),
+                                            ctypes.byref(t)))
+    return {"regs": r.value, "local_bytes": l.value, "static_smem": s_.value, "max_threads": t.value}
+
+
+def hf_src_unload(m):
+    lib.hf_src_unload(m)
