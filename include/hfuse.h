@@ -465,6 +465,20 @@ hf_status hf_src_launch_fused(hf_src_module m, void **params_a, void **params_b,
 hf_status hf_src_query(hf_src_module m, int *regs, int *local_bytes, int *static_smem, int *max_threads);
 void hf_src_unload(hf_src_module m);
 
+/* Device-side failure detection.  Bodies that stage their input through
+ * bulk asynchronous copies wait on them with a time limit (about 2 s); on
+ * expiry the kernel sets a bit in a per-device error word (1 = a bounded
+ * wait expired), waits (bounded) for its copies in flight and stops
+ * consuming, so the context stays usable and the host can detect it.
+ * hf_check_device_error reads the word after the launches have finished
+ * (synchronize the streams first) and clears it when `clear` is set. */
+hf_status hf_check_device_error(unsigned *flags, int clear);
+
+/* Launches one warp that waits on a barrier nothing will complete, with a
+ * limit of limit_us microseconds (1 .. 10^7): it must give up and set bit
+ * 1 of the error word.  Tests the timeout path without any fault. */
+hf_status hf_selftest_wait_timeout(int limit_us, void *stream);
+
 /* Measured throughput of one execution pipe on the current device, for
  * the compute terms of the ideal-overlap bound: what = 0 FP32 fused
  * multiply-adds per second, 1 32-bit integer multiplies (high or low half)

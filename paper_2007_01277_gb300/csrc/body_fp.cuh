@@ -78,6 +78,8 @@ struct BodyBf16Axpy {
     static constexpr int kId = HF_BODY_BF16_AXPY;
     static constexpr int kBarriers = 0;
 
+    static constexpr bool kRing = true;   // streams x and y through a bulk-copy ring
+
     static __host__ size_t workspace_bytes(const Args &) { return 0; }
     static __host__ size_t smem_bytes(int, const Args &) { return 0; }
     static __host__ hf_status validate(const Args &a)
@@ -99,6 +101,11 @@ struct BodyBf16Axpy {
         return pack(__fmaf_rn(al, lo(x), lo(y)), __fmaf_rn(al, hi(x), hi(y)));
     }
 
+    static __device__ __forceinline__ uint4 axpy8(float al, uint4 x, uint4 y)
+    {
+        return make_uint4(axpy2(al, x.x, y.x), axpy2(al, x.y, y.y), axpy2(al, x.z, y.z), axpy2(al, x.w, y.w));
+    }
+
     static __device__ void run(const Args &a, const Ctx &cx)
     {
         const float al = a.alpha;
@@ -107,7 +114,33 @@ struct BodyBf16Axpy {
         int64_t done = 0;
         if (aligned16(a.x) && aligned16(a.y) && aligned16(a.out)) {
             const int64_t n8 = a.n >> 3;
-            int64_t i = gt;
+            int64_t first = 0;   // groups handled by the ring
+            // a tile is half a stage of x groups and half of y groups
+            const int64_t G = cx.ring_stage / 32;   // groups per tensor per tile
+            const int64_t tiles = G ? n8 / G : 0;
+            if (tiles > 0 && WarpRing::available(cx, 0)) {
+                // whole tiles through the bulk-copy ring, one warp per tile
+                WarpRing r;
+                r.init(cx, 0);
+                const int nw = cx.nthreads >> 5;
+                const int64_t gw = (int64_t)cx.block * nw + (cx.tid >> 5), W = (int64_t)cx.grid * nw;
+                const unsigned half = r.bytes / 2;
+                uint4 *out = reinterpret_cast<uint4 *>(a.out);
+                ring_stream(
+                    r, gw, W, tiles,
+                    [&](int st, int64_t t) {
+                        r.expect(st, r.bytes);
+                        r.copy(st, 0, a.x + 8 * G * t, half);
+                        r.copy(st, half, a.y + 8 * G * t, half);
+                    },
+                    [&](const unsigned char *p, int64_t t) {
+                        const uint4 *px = reinterpret_cast<const uint4 *>(p), *py = px + G;
+                        for (int g = r.lane; g < G; g += 32) __stcs(out + G * t + g, axpy8(al, px[g], py[g]));
+                    });
+                r.finish();
+                first = tiles * G;
+            }
+            int64_t i = first + gt;
             for (; i + stride < n8; i += 2 * stride) {
                 const uint4 x0 = ldcs4u(a.x + 8 * i), y0 = ldcs4u(a.y + 8 * i);
                 const uint4 x1 = ldcs4u(a.x + 8 * (i + stride)), y1 = ldcs4u(a.y + 8 * (i + stride));

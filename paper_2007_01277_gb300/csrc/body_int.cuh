@@ -19,6 +19,8 @@ struct BodyHist {
     static constexpr int kId = HF_BODY_HIST256;
     static constexpr int kBarriers = 2;
 
+    static constexpr bool kRing = true;   // streams its bytes through a bulk-copy ring
+
     static __host__ size_t workspace_bytes(const Args &) { return 0; }
     static __host__ size_t smem_bytes(int nthreads, const Args &)
     {
@@ -67,7 +69,30 @@ struct BodyHist {
         if (aligned16(a.x)) {
             const int64_t n16 = a.n >> 4;
             const uint8_t *x = a.x;
-            int64_t i = gt;
+            int64_t first = 0;   // 16-byte groups handled by the ring
+            const int64_t B = cx.ring_stage;   // bytes per tile
+            const int64_t tiles = B ? a.n / B : 0;
+            const size_t counters = (size_t)nw * 256 * sizeof(unsigned);   // a multiple of 128
+            if (tiles > 0 && WarpRing::available(cx, counters)) {
+                // whole tiles through the bulk-copy ring placed after the
+                // counter copies, one warp per tile
+                WarpRing r;
+                r.init(cx, counters);
+                const int64_t gw = (int64_t)cx.block * nw + (cx.tid >> 5), W = (int64_t)cx.grid * nw;
+                ring_stream(
+                    r, gw, W, tiles,
+                    [&](int st, int64_t t) {
+                        r.expect(st, r.bytes);
+                        r.copy(st, 0, x + B * t, r.bytes);
+                    },
+                    [&](const unsigned char *p, int64_t) {
+                        const uint4 *q = reinterpret_cast<const uint4 *>(p);
+                        for (int k = r.lane; k < B / 16; k += 32) count16(mine, q[k]);
+                    });
+                r.finish();
+                first = tiles * (B / 16);
+            }
+            int64_t i = first + gt;
             for (; i + 3 * stride < n16; i += 4 * stride) {
                 uint4 v0 = ldcs4u(x + 16 * i);
                 uint4 v1 = ldcs4u(x + 16 * (i + stride));

@@ -83,6 +83,29 @@ __global__ void k_cal_satom(unsigned *out, int iters)
     if (mine[lane] == 0xffffffffu) out[threadIdx.x] = 1;
 }
 
+// A bounded wait that nothing completes: one warp waits on an mbarrier no
+// copy will ever arrive at, gives up after limit_ns and records
+// kErrWaitExpired.  No copy is in flight, so giving up is safe.
+__global__ void k_selftest_wait(unsigned *err, unsigned long long limit_ns)
+{
+    extern __shared__ __align__(128) unsigned char sm[];
+    hf::Ctx c;
+    c.tid = threadIdx.x;
+    c.nthreads = 32;
+    c.bar = 0;
+    c.block = 0;
+    c.grid = 1;
+    c.smem = sm;
+    c.smem_end = hf::dynamic_smem_end(sm);
+    c.err = err;
+    c.ring_stage = 512;
+    c.ring_stages = 2;
+    hf::WarpRing r;
+    r.init(c, 0, limit_ns);
+    if (!r.wait(0, 0) && threadIdx.x == 0 && err) atomicOr(err, hf::kErrWaitExpired);
+    r.finish();
+}
+
 template <class F>
 hf_status time_ms(F f, cudaStream_t s, float *ms)
 {
@@ -137,5 +160,16 @@ extern "C" hf_status hf_calibrate(int what, void *stream, double *ops_per_s)
         *ops_per_s = (double)blocks * threads * (iters / 4) * 8 / (ms * 1e-3);
     }
     if (st) return hf::set_last_error(st, "calibration kernel failed");
+    return HF_OK;
+}
+
+extern "C" hf_status hf_selftest_wait_timeout(int limit_us, void *stream)
+{
+    if (limit_us <= 0 || limit_us > 10000000) return hf::set_last_error(HF_ERR_INVALID, "limit out of range");
+    const size_t smem = hf::ring_bytes(32, 512, 2);
+    k_selftest_wait<<<1, 32, smem, static_cast<cudaStream_t>(stream)>>>(hf::error_word(),
+                                                                          1000ull * limit_us);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return hf::set_last_error(HF_ERR_CUDA, cudaGetErrorString(e));
     return HF_OK;
 }

@@ -25,7 +25,13 @@ struct Ctx {
     int grid;            // gridDim.x
     unsigned char *smem; // this interval's slice of dynamic shared memory
     unsigned smem_end;   // shared-space address one past the slice
+    unsigned *err;       // the device's error word (bits below), or NULL
+    unsigned ring_stage; // bulk-copy ring of this interval: stage bytes per warp
+    int ring_stages;     //   and stages per warp (0: no ring, use register loads)
 };
+
+// Bits of the device error word read by hf_check_device_error().
+constexpr unsigned kErrWaitExpired = 1u;   // a bounded wait on a bulk copy gave up
 
 // Shared-space address of the start of dynamic shared memory plus its size
 // as launched (the %dynamic_smem_size register).
@@ -89,6 +95,166 @@ __device__ __forceinline__ void stcs2(float *p, float2 v)
 __host__ __device__ __forceinline__ bool aligned16(const void *p)
 {
     return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
+}
+
+} // namespace hf
+
+namespace hf {
+
+// ------------------------------------------------------------------ bulk rings
+// A per-warp ring of S stages in the interval's shared slice, each filled by
+// bulk asynchronous copies (cp.async.bulk, the untiled TMA copy) that signal
+// completion on the stage's mbarrier.  Lane 0 issues the copies; the warp
+// waits on the barrier's phase.  A warp thus keeps several tiles in flight
+// however few warps its interval has: the bandwidth of a memory-bound body
+// inside a fused block no longer depends on its share of the block's
+// warps.
+//
+// The geometry (stage bytes B, stages S) comes from the launch (Ctx): the
+// runtime sizes it for the whole SM -- all ring warps of all resident
+// blocks -- to about 40 KB in flight, where HBM bandwidth peaks; too much
+// in flight costs bandwidth.  Ring layout from `off` in the slice: nw x S
+// stages of B bytes (warp w owns stages [w*S, w*S+S)), then nw x S 8-byte
+// barriers.  Every wait is bounded in time; when it expires the warp sets
+// kErrWaitExpired in the device error word, waits (bounded) for the copies
+// it still has in flight and stops consuming its ring.
+
+__device__ __forceinline__ unsigned long long timer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bytes of a ring of S stages of B bytes for an interval of nthreads.
+__host__ __device__ constexpr size_t ring_bytes(int nthreads, unsigned B, int S)
+{
+    return (size_t)(nthreads / 32) * S * (B + 8);
+}
+
+struct WarpRing {
+    unsigned char *data;    // this warp's stage 0 (generic address)
+    unsigned bars;          // shared address of this warp's barrier 0
+    unsigned bytes;         // stage size
+    int stages, lane;
+    unsigned *err;
+    unsigned long long limit_ns;
+
+    // True when the launch gave this interval a ring that fits its slice
+    // from byte `off` (a multiple of 128).
+    static __device__ bool available(const Ctx &c, size_t off)
+    {
+        return c.ring_stages >= 2 && c.ring_stage >= 512 && c.ring_stage % 128 == 0 &&
+               smem_fits(c, off + ring_bytes(c.nthreads, c.ring_stage, c.ring_stages));
+    }
+    // All lanes of the warp call this, after available() held.  Stages are
+    // 128-byte multiples from a 128-byte aligned start, so every stage is a
+    // valid bulk-copy destination.
+    __device__ void init(const Ctx &c, size_t off, unsigned long long limit = 2000000000ull)
+    {
+        const int nw = c.nthreads >> 5, w = c.tid >> 5;
+        stages = c.ring_stages;
+        const unsigned B = c.ring_stage;
+        bytes = B;
+        lane = c.tid & 31;
+        err = c.err;
+        limit_ns = limit;
+        data = c.smem + off + (size_t)w * stages * B;
+        bars = (unsigned)__cvta_generic_to_shared(c.smem + off + (size_t)nw * stages * B) + 8u * w * stages;
+        if (lane == 0) {
+            for (int s = 0; s < stages; ++s)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bars + 8u * s) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncwarp();
+    }
+    __device__ unsigned char *stage(int s) const { return data + (size_t)s * bytes; }
+
+    // Lane 0: the next phase of stage s completes after `tx` bytes arrive.
+    __device__ void expect(int s, unsigned tx) const
+    {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bars + 8u * s), "r"(tx)
+                     : "memory");
+    }
+    // Lane 0: bulk copy of n bytes (n % 16 == 0, src 16-byte aligned) from
+    // global memory to offset `off` of stage s.
+    __device__ void copy(int s, unsigned off, const void *src, unsigned n) const
+    {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(stage(s)) + off;
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(dst), "l"(src), "r"(n), "r"(bars + 8u * s)
+                     : "memory");
+    }
+    // Lane 0, before refilling a stage the warp has read: order those reads
+    // before the copy engine's writes.
+    __device__ void refill_fence() const { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+    // All lanes: wait for stage s's phase `parity`.  The decision is taken
+    // for the whole warp (vote and lane 0's clock), so lanes never diverge.
+    __device__ bool wait(int s, unsigned parity) const
+    {
+        unsigned long long t0 = 0;
+        for (unsigned it = 0;; ++it) {
+            unsigned done;
+            asm volatile("{\n\t.reg .pred p;\n\t"
+                         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                         "selp.u32 %0, 1, 0, p;\n\t}"
+                         : "=r"(done)
+                         : "r"(bars + 8u * s), "r"(parity)
+                         : "memory");
+            if (__all_sync(0xffffffffu, done)) return true;
+            if ((it & 63u) == 63u) {
+                const unsigned long long now = __shfl_sync(0xffffffffu, timer_ns(), 0);
+                if (t0 == 0) t0 = now;
+                else if (now - t0 > limit_ns) return false;
+            }
+        }
+    }
+    // All lanes, after the last wait: release the barriers' memory.
+    __device__ void finish() const
+    {
+        __syncwarp();
+        if (lane == 0)
+            for (int s = 0; s < stages; ++s)
+                asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bars + 8u * s) : "memory");
+        __syncwarp();
+    }
+};
+
+// Streams tiles first, first + step, ... < count of this warp through the
+// ring: fill(s, t) runs on lane 0 and issues expect() + copy() for tile t
+// into stage s; use(p, t) runs on every lane once the stage has landed.
+// Returns false when a wait expired (error recorded, in-flight copies
+// drained with bounded waits).
+template <class Fill, class Use>
+__device__ bool ring_stream(const WarpRing &r, int64_t first, int64_t step, int64_t count, Fill fill,
+                            Use use)
+{
+    const int S = r.stages;
+    if (r.lane == 0)
+        for (int s = 0; s < S; ++s)
+            if (first + s * step < count) fill(s, first + s * step);
+    int s = 0;
+    unsigned ph = 0;
+    for (int64_t t = first; t < count; t += step) {
+        if (!r.wait(s, ph)) {
+            if (r.lane == 0 && r.err) atomicOr(r.err, kErrWaitExpired);
+            for (int k = 0; k < S; ++k)   // the expired stage included
+                if (t + k * step < count) r.wait((s + k) % S, ph ^ (s + k >= S ? 1u : 0u));
+            return false;
+        }
+        use(r.stage(s), t);
+        __syncwarp();
+        if (r.lane == 0 && t + S * step < count) {
+            r.refill_fence();
+            fill(s, t + S * step);
+        }
+        if (++s == S) {
+            s = 0;
+            ph ^= 1u;
+        }
+    }
+    return true;
 }
 
 } // namespace hf

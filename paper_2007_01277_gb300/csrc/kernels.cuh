@@ -27,6 +27,9 @@ namespace hf {
 template <class B>
 struct SingleParams {
     typename B::Args a;
+    unsigned *err;         // device error word
+    unsigned ring_stage;   // bulk-copy ring geometry chosen by the launch
+    int ring_stages;
 };
 
 template <class B>
@@ -41,6 +44,9 @@ __device__ __forceinline__ void single_body(const SingleParams<B> &p)
     c.grid = gridDim.x;
     c.smem = hf_smem;
     c.smem_end = dynamic_smem_end(hf_smem);
+    c.err = p.err;
+    c.ring_stage = p.ring_stage;
+    c.ring_stages = p.ring_stages;
     B::run(p.a, c);
 }
 
@@ -61,6 +67,9 @@ struct PairParams {
     int n_low, n_high;  // threads in the low / high interval
     unsigned smem_high; // byte offset of the high interval's shared slice
     int low_is_a;       // 1: body A runs on the low interval
+    unsigned *err;      // device error word
+    unsigned ring_stage_low, ring_stage_high;   // ring geometry per interval
+    int ring_stages_low, ring_stages_high;
 };
 
 template <class A, class B>
@@ -71,6 +80,7 @@ __device__ __forceinline__ void pair_body(const PairParams<A, B> &p)
     Ctx c;
     c.block = blockIdx.x;
     c.grid = gridDim.x;
+    c.err = p.err;
     const unsigned end = dynamic_smem_end(hf_smem);
     if (low) {
         c.tid = threadIdx.x;
@@ -78,12 +88,16 @@ __device__ __forceinline__ void pair_body(const PairParams<A, B> &p)
         c.bar = 1;
         c.smem = hf_smem;
         c.smem_end = min(end, (unsigned)__cvta_generic_to_shared(hf_smem) + p.smem_high);
+        c.ring_stage = p.ring_stage_low;
+        c.ring_stages = p.ring_stages_low;
     } else {
         c.tid = threadIdx.x - p.n_low;
         c.nthreads = p.n_high;
         c.bar = 2;
         c.smem = hf_smem + p.smem_high;
         c.smem_end = end;
+        c.ring_stage = p.ring_stage_high;
+        c.ring_stages = p.ring_stages_high;
     }
     if (low == (p.low_is_a != 0))
         A::run(p.a, c);
@@ -115,19 +129,24 @@ struct NwayParams {
     unsigned args_off[HF_MAX_SCHEDULE];         // argument block of slot j in blob
     unsigned char warp_int[32];                 // interval of each warp of the block
     unsigned long long *trace;                  // optional: [n_int][2] first start / last end (ns)
+    unsigned *err;                              // device error word
+    unsigned ring_stage[HF_MAX_INTERVALS];      // ring geometry of interval i
+    int ring_stages[HF_MAX_INTERVALS];
+    // The first polynomial of the schedule also gets its arguments at a
+    // fixed offset of the parameter bank: its coefficients are then
+    // constant-bank operands of the multiply-adds, as in a standalone
+    // launch, instead of registers loaded through a run-time offset.
+    int poly_slot;                              // its slot, or -1
+    hf_poly_args poly;
     alignas(16) unsigned char blob[kNwayBlob];
 };
 
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
+__device__ __forceinline__ unsigned long long global_ns() { return timer_ns(); }
 
-__device__ __forceinline__ void dispatch(int body, const unsigned char *args, const Ctx &c)
+__device__ __forceinline__ void dispatch(const NwayParams &p, int j, const Ctx &c)
 {
-    switch (body) {
+    const unsigned char *args = p.blob + p.args_off[j];
+    switch (p.sched_body[j]) {
     case HF_BODY_BN_STATS: BodyBn::run(*reinterpret_cast<const BodyBn::Args *>(args), c); break;
     case HF_BODY_UPSAMPLE2X:
         BodyUpsample::run(*reinterpret_cast<const BodyUpsample::Args *>(args), c);
@@ -142,7 +161,10 @@ __device__ __forceinline__ void dispatch(int body, const unsigned char *args, co
     case HF_BODY_PHILOX:
         BodyPhilox::run(*reinterpret_cast<const BodyPhilox::Args *>(args), c);
         break;
-    case HF_BODY_POLY: BodyPoly::run(*reinterpret_cast<const BodyPoly::Args *>(args), c); break;
+    case HF_BODY_POLY:
+        if (j == p.poly_slot) BodyPoly::run(p.poly, c);
+        else BodyPoly::run(*reinterpret_cast<const BodyPoly::Args *>(args), c);
+        break;
     case HF_BODY_BF16_AXPY:
         BodyBf16Axpy::run(*reinterpret_cast<const BodyBf16Axpy::Args *>(args), c);
         break;
@@ -180,6 +202,9 @@ __device__ __forceinline__ Ctx interval_ctx(const NwayParams &p, int i)
     c.smem_end = i + 1 < p.n_int
                      ? min(end, (unsigned)__cvta_generic_to_shared(hf_smem) + p.smem_off[i + 1])
                      : end;
+    c.err = p.err;
+    c.ring_stage = p.ring_stage[i];
+    c.ring_stages = p.ring_stages[i];
     return c;
 }
 
@@ -192,7 +217,7 @@ __device__ __forceinline__ void nway_body(const NwayParams &p)
         // kernels sharing an interval share its shared slice: the previous
         // one must be done with it before the next starts
         if (j > j0) interval_sync(interval_ctx(p, i));
-        dispatch(p.sched_body[j], p.blob + p.args_off[j], interval_ctx(p, i));
+        dispatch(p, j, interval_ctx(p, i));
     }
     if (p.trace && (threadIdx.x & 31) == 0) atomicMax(p.trace + 2 * i + 1, global_ns());
 }
@@ -205,12 +230,18 @@ __global__ void __maxnreg__(R) k_nway_cap(const __grid_constant__ NwayParams p)
 }
 
 // ------------------------------------------------------------------ host side
+// The device error word of the current device (runtime.cu), or NULL.
+unsigned *error_word();
+
 struct PairLaunch {
     const void *const *args;   // [0] body A args, [1] body B args
     int w_split, n_low, n_high;
     unsigned smem_high, smem_total;
     int low_is_a;
     int grid, d0;
+    unsigned *err;
+    unsigned ring_stage[2];   // low, high interval
+    int ring_stages[2];
 };
 
 // Registry entry of one compiled instance.
@@ -242,6 +273,11 @@ cudaError_t launch_pair(const PairLaunch &L, cudaStream_t s)
     p.n_high = L.n_high;
     p.smem_high = L.smem_high;
     p.low_is_a = L.low_is_a;
+    p.err = L.err;
+    p.ring_stage_low = L.ring_stage[0];
+    p.ring_stage_high = L.ring_stage[1];
+    p.ring_stages_low = L.ring_stages[0];
+    p.ring_stages_high = L.ring_stages[1];
     void *kargs[] = {&p};
     return cudaLaunchKernel(pair_func<A, B, R>(), dim3(L.grid), dim3(L.d0), kargs, L.smem_total, s);
 }
@@ -264,15 +300,20 @@ const Instance *nway_table(int *n);
 struct SingleEntry {
     int body;
     const void *func;
-    cudaError_t (*launch)(const void *args, int threads, int grid, unsigned smem, cudaStream_t);
+    cudaError_t (*launch)(const void *args, int threads, int grid, unsigned smem, unsigned *err,
+                          unsigned ring_stage, int ring_stages, cudaStream_t);
 };
 
 template <class B>
-cudaError_t launch_single(const void *args, int threads, int grid, unsigned smem, cudaStream_t s)
+cudaError_t launch_single(const void *args, int threads, int grid, unsigned smem, unsigned *err,
+                          unsigned ring_stage, int ring_stages, cudaStream_t s)
 {
     SingleParams<B> p;
     std::memset(&p, 0, sizeof p);
     std::memcpy(&p.a, args, sizeof(typename B::Args));
+    p.err = err;
+    p.ring_stage = ring_stage;
+    p.ring_stages = ring_stages;
     void *kargs[] = {&p};
     return cudaLaunchKernel(reinterpret_cast<const void *>(&k_single<B>), dim3(grid),
                             dim3(threads), kargs, smem, s);

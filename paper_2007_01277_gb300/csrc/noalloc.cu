@@ -13,6 +13,7 @@
 // name is only a host-side stand-in for the symbol.  The device address is
 // looked up with cudaGetSymbolAddress once per device, with that device
 // current, on the first call made there.
+#include <cstring>
 #include <mutex>
 
 #include "kernels.cuh"
@@ -106,7 +107,9 @@ extern "C" hf_status hf_bn_stats_noalloc(const float *x, float *mean, float *var
         grid = per_sm * sms;
     }
     hf::SingleParams<BodyBn> p;
+    std::memset(&p, 0, sizeof p);   // no bulk-copy ring
     p.a = a;
+    p.err = hf::error_word();
     k_bn_noalloc<<<grid, threads, smem, st>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return hf::set_last_error(HF_ERR_CUDA, cudaGetErrorString(e));

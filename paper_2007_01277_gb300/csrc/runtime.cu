@@ -8,6 +8,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <unordered_map>
 #include <vector>
 
@@ -43,7 +44,17 @@ struct BodyOps {
     size_t (*smem)(int, const void *);
     size_t (*workspace)(const void *);
     int barriers;
+    bool ring;   // can stream its input through a bulk-copy ring
     const char *name;
+};
+
+template <class B, class = void>
+struct RingTrait {
+    static constexpr bool value = false;
+};
+template <class B>
+struct RingTrait<B, std::void_t<decltype(B::kRing)>> {
+    static constexpr bool value = B::kRing;
 };
 
 template <class B>
@@ -54,7 +65,7 @@ BodyOps ops(const char *name)
                    [](const void *p) { return B::validate(*static_cast<const A *>(p)); },
                    [](int n, const void *p) { return B::smem_bytes(n, *static_cast<const A *>(p)); },
                    [](const void *p) { return B::workspace_bytes(*static_cast<const A *>(p)); },
-                   B::kBarriers, name};
+                   B::kBarriers, RingTrait<B>::value, name};
 }
 
 const BodyOps &body_ops(int id)
@@ -233,54 +244,118 @@ hf_status check_threads(const hf_kernel_t *k, int t)
     return HF_OK;
 }
 
-struct Geometry {
-    const void *func;
-    unsigned smem_total;
-    int grid;
-};
-
-// Resident blocks of `func` at d0 threads and `smem` bytes -> grid.
-hf_status pick_grid(const void *func, int d0, size_t smem, int want, int *grid, int *bps)
+// Resident blocks of `func` at d0 threads and `smem` bytes (cached, so that
+// a launch recorded into a graph makes no occupancy query).
+hf_status occ_blocks(const void *func, int d0, size_t smem, int *b)
 {
-    hf_device_limits lim;
-    hf_status s = limits(&lim);
+    hf_status s = ensure_smem(func, smem);
     if (s) return s;
-    if (smem > (size_t)lim.smem_per_block_optin)
-        return fail(HF_ERR_SMEM, "combined shared memory %zu B above the %d B per-block limit",
-                    smem, lim.smem_per_block_optin);
-    s = ensure_smem(func, smem);
-    if (s) return s;
-    // resident blocks per (function, block size, shared memory), cached so
-    // that a launch recorded into a graph makes no occupancy query
     static std::mutex occ_mu;
     static std::unordered_map<std::string, int> occ;
     char key[96];
     snprintf(key, sizeof key, "%p/%d/%zu", func, d0, smem);
-    int b = -1;
     {
         std::lock_guard<std::mutex> lk(occ_mu);
         auto it = occ.find(key);
-        if (it != occ.end()) b = it->second;
+        if (it != occ.end()) {
+            *b = it->second;
+            return HF_OK;
+        }
     }
-    if (b < 0) {
-        HF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, func, d0, smem));
-        std::lock_guard<std::mutex> lk(occ_mu);
-        occ[key] = b;
-    }
-    if (b <= 0) return fail(HF_ERR_REGS, "block of %d threads with %zu B shared memory cannot be resident", d0, smem);
-    if (bps) *bps = b;
-    if (grid) *grid = want > 0 ? want : b * lim.sm_count;
+    HF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, func, d0, smem));
+    std::lock_guard<std::mutex> lk(occ_mu);
+    occ[key] = *b;
     return HF_OK;
 }
 
-hf_status pair_smem(const hf_fused_t *f, const void *const *uargs, unsigned *smem_high,
-                    unsigned *total)
+// Bulk-copy ring geometry for `ring_warps` warps per SM that stream through
+// rings: about 40 KB in flight per SM (where HBM bandwidth peaks; more in
+// flight costs bandwidth), in stages of 1, 2 or 4 KB, 2 to 4 stages per
+// warp.  With so many warps that each would keep less than 1 KB in flight,
+// register loads do as well: no ring.
+void ring_geom(int ring_warps, unsigned *stage, int *stages)
 {
-    const size_t lo = align128(body_ops(f->body_low).smem(f->n_low, uargs[0]));
-    const size_t hi = align128(body_ops(f->body_high).smem(f->n_high, uargs[1]));
-    *smem_high = (unsigned)lo;
-    *total = (unsigned)(lo + hi);
-    return HF_OK;
+    *stage = 0;
+    *stages = 0;
+    if (ring_warps <= 0) return;
+    const double F = 40960.0 / ring_warps;   // bytes in flight per warp
+    if (F < 1024.0) return;
+    unsigned B = 1024;
+    while (B < 4096 && 2.0 * B <= F) B *= 2;
+    *stage = B;
+    *stages = std::min(4, std::max(2, 1 + (int)(F / B + 0.5)));
+}
+
+// Shared-memory layout, ring geometry and grid of one launch.
+struct LaunchPlan {
+    unsigned off[HF_MAX_INTERVALS];          // slice offsets
+    unsigned ring_stage[HF_MAX_INTERVALS];   // per interval, 0 = no ring
+    int ring_stages[HF_MAX_INTERVALS];
+    unsigned smem;                           // total dynamic shared memory
+    int grid, bps;
+};
+
+// Plans a launch of `func` with d0 threads cut into n intervals of
+// threads[i] whose kernels need base[i] bytes of shared memory and, where
+// ring[i], a bulk-copy ring after it.  The blocks per SM are the most that
+// stay resident once the rings are sized for that many blocks (or, with an
+// explicit grid `want`, no more than it spreads over the SMs); the grid is
+// `want` or blocks per SM x SMs.
+hf_status plan_launch(const void *func, int d0, int n, const int *threads, const size_t *base,
+                      const bool *ring, int want, LaunchPlan *out)
+{
+    hf_device_limits lim;
+    hf_status s = limits(&lim);
+    if (s) return s;
+    size_t base_total = 0;
+    int ring_w = 0;
+    for (int i = 0; i < n; ++i) {
+        base_total += align128(base[i]);
+        if (ring[i]) ring_w += threads[i] / 32;
+    }
+    if (base_total > (size_t)lim.smem_per_block_optin)
+        return fail(HF_ERR_SMEM, "combined shared memory %zu B above the %d B per-block limit", base_total,
+                    lim.smem_per_block_optin);
+    int bmax = 0;
+    s = occ_blocks(func, d0, base_total, &bmax);
+    if (s) return s;
+    if (bmax <= 0)
+        return fail(HF_ERR_REGS, "block of %d threads with %zu B shared memory cannot be resident", d0,
+                    base_total);
+    if (want > 0) bmax = std::max(1, std::min(bmax, (want + lim.sm_count - 1) / lim.sm_count));
+    for (int b = bmax; b >= 0; --b) {
+        // b == 0: the last resort, no rings at the largest block count
+        unsigned stage = 0;
+        int stages = 0;
+        if (b > 0) ring_geom(b * ring_w, &stage, &stages);
+        size_t off = 0;
+        for (int i = 0; i < n; ++i) {
+            out->off[i] = (unsigned)off;
+            const bool r = ring[i] && stages > 0;
+            out->ring_stage[i] = r ? stage : 0;
+            out->ring_stages[i] = r ? stages : 0;
+            off += align128(align128(base[i]) + (r ? ring_bytes(threads[i], stage, stages) : 0));
+        }
+        if (off > (size_t)lim.smem_per_block_optin) continue;
+        int got = 0;
+        s = occ_blocks(func, d0, off, &got);
+        if (s) return s;
+        if (got >= std::max(b, 1)) {
+            out->smem = (unsigned)off;
+            out->bps = b > 0 ? b : bmax;
+            out->grid = want > 0 ? want : out->bps * lim.sm_count;
+            return HF_OK;
+        }
+    }
+    return fail(HF_ERR_REGS, "no resident configuration for a block of %d threads", d0);
+}
+
+hf_status single_plan(const hf_kernel_t *k, const void *args, int threads, int want, LaunchPlan *plan)
+{
+    const SingleEntry *e = find_single(k->body);
+    const size_t base = body_ops(k->body).smem(threads, args);
+    const bool ring = body_ops(k->body).ring;
+    return plan_launch(e->func, threads, 1, &threads, &base, &ring, want, plan);
 }
 
 hf_status validate_args(int body, const void *a, int which)
@@ -293,21 +368,24 @@ hf_status validate_args(int body, const void *a, int which)
 
 // Builds the N-way parameter block; also used for pairs without a compiled
 // pair instance.
-hf_status nway_params(const hf_fused_t *f, const void *const *args, NwayParams *p, unsigned *smem)
+hf_status nway_params(const hf_fused_t *f, const void *const *args, int want, NwayParams *p,
+                      LaunchPlan *plan)
 {
     std::memset(p, 0, sizeof *p);
     p->n_int = f->n_int;
     int w = 0;
-    size_t off = 0;
+    size_t base[HF_MAX_INTERVALS];
+    bool ring[HF_MAX_INTERVALS];
     for (int i = 0; i < f->n_int; ++i) {
         p->warp_begin[i] = w;
         w += f->int_threads[i] / 32;
-        size_t need = 0;
+        base[i] = 0;
+        ring[i] = false;
         for (int j = 0; j < f->n; ++j)
-            if (f->sched_int[j] == i)
-                need = std::max(need, body_ops(f->sched_body[j]).smem(f->int_threads[i], args[j]));
-        p->smem_off[i] = (unsigned)off;
-        off += align128(need);
+            if (f->sched_int[j] == i) {
+                base[i] = std::max(base[i], body_ops(f->sched_body[j]).smem(f->int_threads[i], args[j]));
+                ring[i] = ring[i] || body_ops(f->sched_body[j]).ring;
+            }
     }
     p->warp_begin[f->n_int] = w;
     for (int i = 0; i < f->n_int; ++i)
@@ -316,6 +394,7 @@ hf_status nway_params(const hf_fused_t *f, const void *const *args, NwayParams *
     // caller's order
     size_t boff = 0;
     int slot = 0;
+    p->poly_slot = -1;
     for (int i = 0; i < f->n_int; ++i) {
         p->int_first[i] = slot;
         for (int j = 0; j < f->n; ++j) {
@@ -325,6 +404,10 @@ hf_status nway_params(const hf_fused_t *f, const void *const *args, NwayParams *
             if (boff + sz > (size_t)kNwayBlob)
                 return fail(HF_ERR_INVALID, "argument blocks exceed %d B", kNwayBlob);
             std::memcpy(p->blob + boff, args[j], sz);
+            if (f->sched_body[j] == HF_BODY_POLY && p->poly_slot < 0) {
+                p->poly_slot = slot;
+                std::memcpy(&p->poly, args[j], sizeof p->poly);
+            }
             p->sched_body[slot] = f->sched_body[j];
             p->args_off[slot] = (unsigned)boff;
             boff += sz;
@@ -332,18 +415,70 @@ hf_status nway_params(const hf_fused_t *f, const void *const *args, NwayParams *
         }
     }
     p->int_first[f->n_int] = slot;
-    *smem = (unsigned)off;
+    hf_status s = plan_launch(f->inst->func, f->d0, f->n_int, f->int_threads, base, ring, want, plan);
+    if (s) return s;
+    for (int i = 0; i < f->n_int; ++i) {
+        p->smem_off[i] = plan->off[i];
+        p->ring_stage[i] = plan->ring_stage[i];
+        p->ring_stages[i] = plan->ring_stages[i];
+    }
     return HF_OK;
+}
+
+// Plans a 2-way fused launch.
+hf_status pair_plan(const hf_fused_t *f, const void *const *uargs, int want, LaunchPlan *plan)
+{
+    const int threads[2] = {f->n_low, f->n_high};
+    const size_t base[2] = {body_ops(f->body_low).smem(f->n_low, uargs[0]),
+                            body_ops(f->body_high).smem(f->n_high, uargs[1])};
+    const bool ring[2] = {body_ops(f->body_low).ring, body_ops(f->body_high).ring};
+    return plan_launch(f->inst->func, f->d0, 2, threads, base, ring, want, plan);
 }
 } // namespace
 
 // Records a one-line error for hf_last_error() from other translation units.
 namespace hf {
 hf_status set_last_error(hf_status s, const char *msg) { return fail(s, "%s", msg); }
+
+// The device error word: a file-scope device variable (no allocation),
+// its address looked up once per device.
+static __device__ unsigned g_hf_error_word;
+
+unsigned *error_word()
+{
+    static std::mutex mu;
+    static unsigned *addr[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_hf_error_word) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        addr[dev] = static_cast<unsigned *>(p);
+    }
+    return addr[dev];
+}
 } // namespace hf
 
 // ------------------------------------------------------------------ C ABI
 extern "C" {
+
+hf_status hf_check_device_error(unsigned *flags, int clear)
+{
+    if (!flags) return fail(HF_ERR_INVALID, "NULL flags");
+    HF_CUDA(cudaMemcpyFromSymbol(flags, hf::g_hf_error_word, sizeof(unsigned)));
+    if (clear && *flags) {
+        const unsigned z = 0;
+        HF_CUDA(cudaMemcpyToSymbol(hf::g_hf_error_word, &z, sizeof z));
+    }
+    return HF_OK;
+}
 
 const char *hf_status_string(hf_status s)
 {
@@ -530,13 +665,13 @@ static hf_status launch_impl(hf_fused f, const void *const *args, int grid, void
         if (s) return s;
         s = validate_args(f->body_high, args[1], 1);
         if (s) return s;
-        unsigned smem_high, total;
-        pair_smem(f, args, &smem_high, &total);
-        int g = 0;
-        s = pick_grid(f->inst->func, f->d0, total, grid, &g, nullptr);
-        if (s) return s;
         const void *iargs[2] = {f->low_is_a ? args[0] : args[1], f->low_is_a ? args[1] : args[0]};
-        PairLaunch L{iargs, f->n_low / 32, f->n_low, f->n_high, smem_high, total, f->low_is_a, g, f->d0};
+        LaunchPlan plan;
+        s = pair_plan(f, iargs, grid, &plan);
+        if (s) return s;
+        PairLaunch L{iargs, f->n_low / 32, f->n_low, f->n_high, plan.off[1], plan.smem, f->low_is_a,
+                     plan.grid, f->d0, hf::error_word(), {plan.ring_stage[0], plan.ring_stage[1]},
+                     {plan.ring_stages[0], plan.ring_stages[1]}};
         HF_CUDA(f->inst->launch_pair(L, st));
         return HF_OK;
     }
@@ -545,15 +680,13 @@ static hf_status launch_impl(hf_fused f, const void *const *args, int grid, void
         if (s) return s;
     }
     static thread_local NwayParams p;
-    unsigned smem = 0;
-    hf_status s = nway_params(f, args, &p, &smem);
+    LaunchPlan plan;
+    hf_status s = nway_params(f, args, grid, &p, &plan);
     if (s) return s;
     p.trace = trace;
-    int g = 0;
-    s = pick_grid(f->inst->func, f->d0, smem, grid, &g, nullptr);
-    if (s) return s;
+    p.err = hf::error_word();
     void *kargs[] = {&p};
-    HF_CUDA(cudaLaunchKernel(f->inst->func, dim3(g), dim3(f->d0), kargs, smem, st));
+    HF_CUDA(cudaLaunchKernel(f->inst->func, dim3(plan.grid), dim3(f->d0), kargs, plan.smem, st));
     return HF_OK;
 }
 
@@ -566,37 +699,37 @@ hf_status hf_launch_single(hf_kernel k, const void *args, int threads, int grid,
     s = validate_args(k->body, args, 0);
     if (s) return s;
     const SingleEntry *e = find_single(k->body);
-    const size_t smem = align128(body_ops(k->body).smem(threads, args));
     FuncInfo fi;
     s = func_info(e->func, &fi);
     if (s) return s;
     if (fi.max_threads < threads)
         return fail(HF_ERR_REGS, "kernel uses %d registers: at most %d threads", fi.regs, fi.max_threads);
-    int g = 0;
-    s = pick_grid(e->func, threads, smem, grid, &g, nullptr);
+    LaunchPlan plan;
+    s = single_plan(k, args, threads, grid, &plan);
     if (s) return s;
-    HF_CUDA(e->launch(args, threads, g, (unsigned)smem, static_cast<cudaStream_t>(stream)));
+    HF_CUDA(e->launch(args, threads, plan.grid, plan.smem, hf::error_word(), plan.ring_stage[0],
+                      plan.ring_stages[0], static_cast<cudaStream_t>(stream)));
     return HF_OK;
 }
 
 hf_status hf_query(hf_fused f, const void *const *args, hf_fused_info *info)
 {
     if (!f || !args || !info) return fail(HF_ERR_INVALID, "NULL argument");
-    unsigned smem = 0;
+    LaunchPlan plan;
     if (!f->nway) {
-        unsigned hi;
-        pair_smem(f, args, &hi, &smem);
+        const void *iargs[2] = {f->low_is_a ? args[0] : args[1], f->low_is_a ? args[1] : args[0]};
+        hf_status s = pair_plan(f, iargs, 0, &plan);
+        if (s) return s;
     } else {
         static thread_local NwayParams p;
-        hf_status s = nway_params(f, args, &p, &smem);
+        hf_status s = nway_params(f, args, 0, &p, &plan);
         if (s) return s;
     }
     FuncInfo fi;
     hf_status s = func_info(f->inst->func, &fi);
     if (s) return s;
-    int bps = 0;
-    s = pick_grid(f->inst->func, f->d0, smem, 0, nullptr, &bps);
-    if (s) return s;
+    const unsigned smem = plan.smem;
+    const int bps = plan.bps;
     info->regs = fi.regs;
     info->spill_bytes = fi.local;
     info->smem_bytes = (int)smem;
@@ -613,13 +746,14 @@ hf_status hf_query_single(hf_kernel k, const void *args, int threads, hf_fused_i
     hf_status s = check_threads(k, threads);
     if (s) return s;
     const SingleEntry *e = find_single(k->body);
-    const size_t smem = align128(body_ops(k->body).smem(threads, args));
     FuncInfo fi;
     s = func_info(e->func, &fi);
     if (s) return s;
-    int bps = 0;
-    s = pick_grid(e->func, threads, smem, 0, nullptr, &bps);
+    LaunchPlan plan;
+    s = single_plan(k, args, threads, 0, &plan);
     if (s) return s;
+    const size_t smem = plan.smem;
+    const int bps = plan.bps;
     info->regs = fi.regs;
     info->spill_bytes = fi.local;
     info->smem_bytes = (int)smem;

@@ -176,6 +176,8 @@ def _load():
         "hf_src_query": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                                 ctypes.POINTER(_i32)]),
         "hf_src_unload": (None, [_P]),
+        "hf_check_device_error": (_i32, [ctypes.POINTER(ctypes.c_uint), _i32]),
+        "hf_selftest_wait_timeout": (_i32, [_i32, _P]),
         "hf_tmpl_features": (_i32, [ctypes.POINTER(StreamTmplArgs), ctypes.POINTER(StreamTmplArgs),
                                     _i32, _i32, _i32, _i32, _i32, _i32, ctypes.c_double,
                                     ctypes.c_double, ctypes.POINTER(_f32)]),
@@ -586,3 +588,18 @@ def hf_src_query(m):
 
 def hf_src_unload(m):
     lib.hf_src_unload(m)
+
+
+# ----------------------------------------------------------------- device errors
+ERR_WAIT_EXPIRED = 1
+
+
+def hf_check_device_error(clear=False):
+    """The device error word (read after the launches have finished)."""
+    v = ctypes.c_uint()
+    _check("hf_check_device_error", lib.hf_check_device_error(ctypes.byref(v), int(clear)))
+    return v.value
+
+
+def hf_selftest_wait_timeout(limit_us, stream=None):
+    _check("hf_selftest_wait_timeout", lib.hf_selftest_wait_timeout(limit_us, _stream_ptr(stream)))

@@ -90,13 +90,14 @@ def test_im2col(shape, threads, grid):
 
 @pytest.mark.parametrize("n,offset", [(0, 0), (1, 0), (15, 0), (16, 0), (17, 0), (1000003, 0),
                                       (100000, 1), (5 << 20, 0)])
-@pytest.mark.parametrize("threads,grid", [(256, 0), (128, 3)])
+@pytest.mark.parametrize("threads,grid", [(256, 0), (128, 3), (1024, 5)])
 def test_hist(n, offset, threads, grid):
     x = W.hist_input(n + offset, seed=n)
     xd = x.to(DEV)[offset:]
     bins = torch.zeros(256, dtype=torch.int32, device=DEV)
     single(H.HIST256, H.hist256_args(xd, bins), threads, grid)
     torch.cuda.synchronize()
+    assert H.hf_check_device_error() == 0
     ref = oracle.hist256(x.numpy()[offset:])
     assert np.array_equal(bins.cpu().numpy().view(np.uint32), ref)
 
@@ -125,14 +126,15 @@ def test_poly(n, offset, iters, threads, grid):
     check_poly(x[offset:], coef, y, iters)
 
 
-@pytest.mark.parametrize("n,offset", [(1, 0), (9, 0), (100003, 0), (4096, 1)])
-@pytest.mark.parametrize("threads,grid", [(256, 0), (64, 3)])
+@pytest.mark.parametrize("n,offset", [(1, 0), (9, 0), (100003, 0), (4096, 1), ((1 << 21) + 40, 0)])
+@pytest.mark.parametrize("threads,grid", [(256, 0), (64, 3), (1024, 2)])
 def test_bf16_axpy(n, offset, threads, grid):
     x, y = W.bf16_inputs(n + offset, seed=n)
     xd, yd = x.to(DEV)[offset:], y.to(DEV)[offset:]
     out = torch.empty(n + offset, dtype=torch.bfloat16, device=DEV)[offset:]
     single(H.BF16_AXPY, H.bf16_axpy_args(xd, yd, out, 0.5), threads, grid)
     torch.cuda.synchronize()
+    assert H.hf_check_device_error() == 0
     assert check_bf16(x[offset:], y[offset:], out) == 0
 
 

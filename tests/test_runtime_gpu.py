@@ -118,3 +118,18 @@ def test_stream_wait_times_out_on_long_kernel():
         H.hf_stream_wait(s, 1)
     assert e.value.status == -8
     H.hf_stream_wait(s, 60000)
+
+
+def test_bounded_wait_expires_and_sets_the_error_word():
+    """A device-side wait that nothing completes gives up after its limit and
+    reports it through the error word; the context stays usable."""
+    torch.cuda.synchronize()
+    H.hf_check_device_error(clear=True)
+    H.hf_selftest_wait_timeout(2000)
+    torch.cuda.synchronize()
+    assert H.hf_check_device_error(clear=True) & H.ERR_WAIT_EXPIRED
+    assert H.hf_check_device_error() == 0
+    x = torch.arange(1024, dtype=torch.float32, device="cuda")
+    assert float(x.sum().item()) == 1023 * 1024 / 2
+    with pytest.raises(H.HFError):
+        H.hf_selftest_wait_timeout(0)
