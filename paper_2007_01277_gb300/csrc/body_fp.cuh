@@ -78,7 +78,11 @@ struct BodyBf16Axpy {
     static constexpr int kId = HF_BODY_BF16_AXPY;
     static constexpr int kBarriers = 0;
 
-    static constexpr bool kRing = true;   // streams x and y through a bulk-copy ring
+    // whole tiles of x and y stream through a bulk-copy ring
+    static __host__ bool uses_ring(const Args &a)
+    {
+        return a.n >= 8 * 32 && aligned16(a.x) && aligned16(a.y) && aligned16(a.out);
+    }
 
     static __host__ size_t workspace_bytes(const Args &) { return 0; }
     static __host__ size_t smem_bytes(int, const Args &) { return 0; }

@@ -19,7 +19,8 @@ struct BodyHist {
     static constexpr int kId = HF_BODY_HIST256;
     static constexpr int kBarriers = 2;
 
-    static constexpr bool kRing = true;   // streams its bytes through a bulk-copy ring
+    // whole tiles of bytes stream through a bulk-copy ring
+    static __host__ bool uses_ring(const Args &a) { return a.n >= 512 && aligned16(a.x); }
 
     static __host__ size_t workspace_bytes(const Args &) { return 0; }
     static __host__ size_t smem_bytes(int nthreads, const Args &)

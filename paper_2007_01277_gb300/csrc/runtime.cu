@@ -44,17 +44,27 @@ struct BodyOps {
     size_t (*smem)(int, const void *);
     size_t (*workspace)(const void *);
     int barriers;
-    bool ring;   // can stream its input through a bulk-copy ring
+    bool (*ring)(const void *);   // will stream these arguments through a bulk-copy ring
+    unsigned ring_min;            // ...if each warp keeps at least this many bytes in flight
     const char *name;
 };
 
+// Bodies with a ring path declare `static bool uses_ring(const Args &)`.
 template <class B, class = void>
 struct RingTrait {
-    static constexpr bool value = false;
+    static bool uses(const void *) { return false; }
 };
 template <class B>
-struct RingTrait<B, std::void_t<decltype(B::kRing)>> {
-    static constexpr bool value = B::kRing;
+struct RingTrait<B, std::void_t<decltype(B::uses_ring(std::declval<const typename B::Args &>()))>> {
+    static bool uses(const void *p) { return B::uses_ring(*static_cast<const typename B::Args *>(p)); }
+};
+template <class B, class = void>
+struct RingMin {
+    static constexpr unsigned value = 1024;
+};
+template <class B>
+struct RingMin<B, std::void_t<decltype(B::kRingMinBytes)>> {
+    static constexpr unsigned value = B::kRingMinBytes;
 };
 
 template <class B>
@@ -65,7 +75,7 @@ BodyOps ops(const char *name)
                    [](const void *p) { return B::validate(*static_cast<const A *>(p)); },
                    [](int n, const void *p) { return B::smem_bytes(n, *static_cast<const A *>(p)); },
                    [](const void *p) { return B::workspace_bytes(*static_cast<const A *>(p)); },
-                   B::kBarriers, RingTrait<B>::value, name};
+                   B::kBarriers, &RingTrait<B>::uses, RingMin<B>::value, name};
 }
 
 const BodyOps &body_ops(int id)
@@ -268,17 +278,14 @@ hf_status occ_blocks(const void *func, int d0, size_t smem, int *b)
     return HF_OK;
 }
 
-// Bulk-copy ring geometry for `ring_warps` warps per SM that stream through
-// rings: about 40 KB in flight per SM (where HBM bandwidth peaks; more in
-// flight costs bandwidth), in stages of 1, 2 or 4 KB, 2 to 4 stages per
-// warp.  With so many warps that each would keep less than 1 KB in flight,
-// register loads do as well: no ring.
-void ring_geom(int ring_warps, unsigned *stage, int *stages)
+// Bulk-copy ring geometry for F bytes in flight per warp (about 40 KB per
+// SM over the SM's ring warps, where HBM bandwidth peaks; more in flight
+// costs bandwidth): stages of 1, 2 or 4 KB, 2 to 4 per warp.  Below 1 KB
+// per warp register loads do as well: no ring.
+void ring_geom(double F, unsigned *stage, int *stages)
 {
     *stage = 0;
     *stages = 0;
-    if (ring_warps <= 0) return;
-    const double F = 40960.0 / ring_warps;   // bytes in flight per warp
     if (F < 1024.0) return;
     unsigned B = 1024;
     while (B < 4096 && 2.0 * B <= F) B *= 2;
@@ -302,7 +309,7 @@ struct LaunchPlan {
 // explicit grid `want`, no more than it spreads over the SMs); the grid is
 // `want` or blocks per SM x SMs.
 hf_status plan_launch(const void *func, int d0, int n, const int *threads, const size_t *base,
-                      const bool *ring, int want, LaunchPlan *out)
+                      const bool *ring, const unsigned *ring_min, int want, LaunchPlan *out)
 {
     hf_device_limits lim;
     hf_status s = limits(&lim);
@@ -324,14 +331,29 @@ hf_status plan_launch(const void *func, int d0, int n, const int *threads, const
                     base_total);
     if (want > 0) bmax = std::max(1, std::min(bmax, (want + lim.sm_count - 1) / lim.sm_count));
     for (int b = bmax; b >= 0; --b) {
-        // b == 0: the last resort, no rings at the largest block count
+        // b == 0: the last resort, no rings at the largest block count.
+        // Intervals whose body wants more in flight per warp than the SM's
+        // share gives drop their ring (register loads), and the share is
+        // recomputed over the rest.
+        bool use[HF_MAX_INTERVALS];
+        for (int i = 0; i < n; ++i) use[i] = ring[i] && b > 0;
+        double F = 0.0;
+        for (bool changed = true; changed;) {
+            changed = false;
+            int w = 0;
+            for (int i = 0; i < n; ++i)
+                if (use[i]) w += threads[i] / 32;
+            F = w > 0 ? 40960.0 / ((double)b * w) : 0.0;
+            for (int i = 0; i < n; ++i)
+                if (use[i] && F < ring_min[i]) use[i] = false, changed = true;
+        }
         unsigned stage = 0;
         int stages = 0;
-        if (b > 0) ring_geom(b * ring_w, &stage, &stages);
+        ring_geom(F, &stage, &stages);
         size_t off = 0;
         for (int i = 0; i < n; ++i) {
             out->off[i] = (unsigned)off;
-            const bool r = ring[i] && stages > 0;
+            const bool r = use[i] && stages > 0;
             out->ring_stage[i] = r ? stage : 0;
             out->ring_stages[i] = r ? stages : 0;
             off += align128(align128(base[i]) + (r ? ring_bytes(threads[i], stage, stages) : 0));
@@ -354,8 +376,9 @@ hf_status single_plan(const hf_kernel_t *k, const void *args, int threads, int w
 {
     const SingleEntry *e = find_single(k->body);
     const size_t base = body_ops(k->body).smem(threads, args);
-    const bool ring = body_ops(k->body).ring;
-    return plan_launch(e->func, threads, 1, &threads, &base, &ring, want, plan);
+    const bool ring = body_ops(k->body).ring(args);
+    const unsigned ring_min = body_ops(k->body).ring_min;
+    return plan_launch(e->func, threads, 1, &threads, &base, &ring, &ring_min, want, plan);
 }
 
 hf_status validate_args(int body, const void *a, int which)
@@ -376,15 +399,21 @@ hf_status nway_params(const hf_fused_t *f, const void *const *args, int want, Nw
     int w = 0;
     size_t base[HF_MAX_INTERVALS];
     bool ring[HF_MAX_INTERVALS];
+    unsigned ring_min[HF_MAX_INTERVALS];
     for (int i = 0; i < f->n_int; ++i) {
         p->warp_begin[i] = w;
         w += f->int_threads[i] / 32;
         base[i] = 0;
         ring[i] = false;
+        ring_min[i] = 0;
         for (int j = 0; j < f->n; ++j)
             if (f->sched_int[j] == i) {
-                base[i] = std::max(base[i], body_ops(f->sched_body[j]).smem(f->int_threads[i], args[j]));
-                ring[i] = ring[i] || body_ops(f->sched_body[j]).ring;
+                const BodyOps &o = body_ops(f->sched_body[j]);
+                base[i] = std::max(base[i], o.smem(f->int_threads[i], args[j]));
+                if (o.ring(args[j])) {
+                    ring[i] = true;
+                    ring_min[i] = std::max(ring_min[i], o.ring_min);
+                }
             }
     }
     p->warp_begin[f->n_int] = w;
@@ -415,7 +444,8 @@ hf_status nway_params(const hf_fused_t *f, const void *const *args, int want, Nw
         }
     }
     p->int_first[f->n_int] = slot;
-    hf_status s = plan_launch(f->inst->func, f->d0, f->n_int, f->int_threads, base, ring, want, plan);
+    hf_status s = plan_launch(f->inst->func, f->d0, f->n_int, f->int_threads, base, ring, ring_min, want,
+                              plan);
     if (s) return s;
     for (int i = 0; i < f->n_int; ++i) {
         p->smem_off[i] = plan->off[i];
@@ -431,8 +461,9 @@ hf_status pair_plan(const hf_fused_t *f, const void *const *uargs, int want, Lau
     const int threads[2] = {f->n_low, f->n_high};
     const size_t base[2] = {body_ops(f->body_low).smem(f->n_low, uargs[0]),
                             body_ops(f->body_high).smem(f->n_high, uargs[1])};
-    const bool ring[2] = {body_ops(f->body_low).ring, body_ops(f->body_high).ring};
-    return plan_launch(f->inst->func, f->d0, 2, threads, base, ring, want, plan);
+    const bool ring[2] = {body_ops(f->body_low).ring(uargs[0]), body_ops(f->body_high).ring(uargs[1])};
+    const unsigned ring_min[2] = {body_ops(f->body_low).ring_min, body_ops(f->body_high).ring_min};
+    return plan_launch(f->inst->func, f->d0, 2, threads, base, ring, ring_min, want, plan);
 }
 } // namespace
 

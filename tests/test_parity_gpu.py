@@ -51,20 +51,22 @@ def test_bn_offset_mean_and_constant_channel():
 
 
 @pytest.mark.parametrize("shape", [(2, 3, 20, 24), (1, 2, 9, 7), (2, 2, 128, 128), (1, 1, 10, 260),
-                                   (1, 1, 1, 1), (3, 1, 17, 4)])
-@pytest.mark.parametrize("threads,grid", [(256, 0), (96, 5)])
+                                   (1, 1, 1, 1), (3, 1, 17, 4), (2, 3, 37, 36), (1, 1, 1, 128)])
+@pytest.mark.parametrize("threads,grid", [(256, 0), (96, 5), (512, 3), (32, 1)])
 def test_upsample(shape, threads, grid):
     x = W.upsample_input(shape, seed=sum(shape))
     xd = x.to(DEV)
     y = torch.empty(shape[:-2] + (2 * shape[-2], 2 * shape[-1]), device=DEV)
     single(H.UPSAMPLE2X, H.upsample2x_args(xd, y), threads, grid)
     torch.cuda.synchronize()
+    assert H.hf_check_device_error() == 0
     check_upsample(x, y)
 
 
 @pytest.mark.parametrize("shape", [(2, 3, 20, 24), (1, 2, 9, 7), (2, 4, 112, 112), (1, 1, 11, 264),
-                                   (1, 1, 1, 1), (2, 1, 2, 4)])
-@pytest.mark.parametrize("threads,grid", [(256, 0), (96, 5)])
+                                   (1, 1, 1, 1), (2, 1, 2, 4), (3, 2, 37, 36), (1, 3, 57, 128),
+                                   (1, 1, 1, 8), (2, 1, 3, 4)])
+@pytest.mark.parametrize("threads,grid", [(256, 0), (96, 5), (768, 3), (32, 1)])
 def test_maxpool(shape, threads, grid):
     x = W.maxpool_input(shape, seed=sum(shape))
     xd = x.to(DEV)
@@ -72,6 +74,7 @@ def test_maxpool(shape, threads, grid):
     y = torch.empty(shape[:-2] + ((H_ - 1) // 2 + 1, (W_ - 1) // 2 + 1), device=DEV)
     single(H.MAXPOOL3S2, H.maxpool3s2_args(xd, y), threads, grid)
     torch.cuda.synchronize()
+    assert H.hf_check_device_error() == 0
     assert np.array_equal(y.cpu().numpy(), oracle.maxpool3s2p1(x.numpy()))
 
 
