@@ -20,7 +20,8 @@ from paper_2007_01277_gb300 import workloads as W  # noqa: E402
 
 # ------------------------------------------------------------------ standalone vs oracle
 @pytest.mark.parametrize("shape", [(2, 8, 16, 12), (3, 5, 7, 9), (8, 4, 40, 40), (8, 64, 32, 32),
-                                   (1, 1, 1, 4), (5, 3, 1, 2050)])
+                                   (1, 1, 1, 4), (5, 3, 1, 2050), (3, 5, 56, 56), (2, 3, 33, 36),
+                                   (1, 2, 64, 64)])
 @pytest.mark.parametrize("threads,grid", [(256, 0), (64, 3), (1024, 1)])
 def test_bn_stats(shape, threads, grid):
     x = W.bn_input(shape, seed=sum(shape))
@@ -37,6 +38,25 @@ def test_bn_stats(shape, threads, grid):
     single(H.BN_STATS, H.bn_stats_args(xd, m2, v2, ws), threads, grid)
     torch.cuda.synchronize()
     assert torch.equal(mean, m2) and torch.equal(var, v2)
+
+
+@pytest.mark.parametrize("shape", [(3, 5, 56, 56), (8, 64, 32, 32), (2, 3, 33, 36)])
+def test_bn_bits_independent_of_launch(shape):
+    """Each 2048-value tile is reduced by one warp in a fixed order and the
+    tiles combine in tile order, so every launch configuration gives the
+    same bits."""
+    x = W.bn_input(shape, seed=7).to(DEV)
+    C = shape[1]
+    ws = H.bn_stats_workspace(x)
+    outs = []
+    for threads, grid in ((256, 0), (64, 3), (1024, 1), (128, 40), (32, 152)):
+        m, v = torch.empty(C, device=DEV), torch.empty(C, device=DEV)
+        single(H.BN_STATS, H.bn_stats_args(x, m, v, ws), threads, grid)
+        torch.cuda.synchronize()
+        outs.append((m, v))
+    assert H.hf_check_device_error() == 0
+    for m, v in outs[1:]:
+        assert torch.equal(m, outs[0][0]) and torch.equal(v, outs[0][1])
 
 
 def test_bn_offset_mean_and_constant_channel():
