@@ -354,6 +354,17 @@ hf_status hf_search_alg2(hf_kernel a, hf_kernel b, const void *const *args, int 
                          int reps, int flush_l2, void *stream, hf_tune_point *best,
                          hf_tune_point *trace, int trace_cap, int *n_trace);
 
+/* One call that tunes a pair for a d0-thread block and returns the point
+ * to launch: mode HF_TUNE_EXHAUSTIVE profiles every split in warp steps
+ * (32 .. d0 - 32, within both kernels' thread ranges) x every compiled
+ * register cap and "none" x 1..4 blocks per SM and takes the fastest;
+ * mode HF_TUNE_ALG2 runs hf_search_alg2 with step 128 (64 for d0 < 512).
+ * Timing as hf_time_fused (reps launches, L2 flushed when flush_l2).
+ * HF_ERR_INVALID for an unknown mode or when no point can be launched. */
+enum { HF_TUNE_EXHAUSTIVE = 0, HF_TUNE_ALG2 = 1 };
+hf_status hf_autotune(hf_kernel a, hf_kernel b, const void *const *args, int d0, int mode, int reps,
+                      int flush_l2, void *stream, hf_tune_point *best);
+
 /* ------------------------------------------------------------------ */
 /* Allocation-free batch-norm statistics.                               */
 

@@ -499,3 +499,30 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
 }
 
 } // extern "C"
+
+extern "C" hf_status hf_autotune(hf_kernel a, hf_kernel b, const void *const *args, int d0, int mode,
+                                 int reps, int flush_l2_, void *stream, hf_tune_point *best)
+{
+    if (!a || !b || !args || !best || reps < 1) return HF_ERR_INVALID;
+    if (mode == HF_TUNE_ALG2)
+        return hf_search_alg2(a, b, args, d0, d0 >= 512 ? 128 : 64, reps, flush_l2_, stream, best,
+                              nullptr, 0, nullptr);
+    if (mode != HF_TUNE_EXHAUSTIVE || d0 < 64 || d0 > 1024 || d0 % 32) return HF_ERR_INVALID;
+    std::vector<int> splits, caps = {0}, bps = {1, 2, 3, 4};
+    for (int s = 32; s < d0; s += 32) splits.push_back(s);
+    int nc = hf_regcaps(nullptr, 0);
+    std::vector<int> compiled(nc > 0 ? nc : 0);
+    if (nc > 0) hf_regcaps(compiled.data(), nc);
+    caps.insert(caps.end(), compiled.begin(), compiled.end());
+    std::vector<hf_tune_point> table(splits.size() * caps.size() * bps.size());
+    hf_status st = hf_profile_pair(a, b, args, d0, splits.data(), (int)splits.size(), caps.data(),
+                                   (int)caps.size(), bps.data(), (int)bps.size(), reps, flush_l2_, stream,
+                                   table.data());
+    if (st) return st;
+    const hf_tune_point *pick = nullptr;
+    for (const hf_tune_point &p : table)
+        if (p.status == HF_OK && (!pick || p.time_us < pick->time_us)) pick = &p;
+    if (!pick) return HF_ERR_INVALID;
+    *best = *pick;
+    return HF_OK;
+}

@@ -177,6 +177,8 @@ def _load():
                                 ctypes.POINTER(_i32)]),
         "hf_src_unload": (None, [_P]),
         "hf_check_device_error": (_i32, [ctypes.POINTER(ctypes.c_uint), _i32]),
+        "hf_autotune": (_i32, [_P, _P, ctypes.POINTER(_P), _i32, _i32, _i32, _i32, _P,
+                               ctypes.POINTER(TunePoint)]),
         "hf_selftest_wait_timeout": (_i32, [_i32, _P]),
         "hf_tmpl_features": (_i32, [ctypes.POINTER(StreamTmplArgs), ctypes.POINTER(StreamTmplArgs),
                                     _i32, _i32, _i32, _i32, _i32, _i32, ctypes.c_double,
@@ -603,3 +605,15 @@ def hf_check_device_error(clear=False):
 
 def hf_selftest_wait_timeout(limit_us, stream=None):
     _check("hf_selftest_wait_timeout", lib.hf_selftest_wait_timeout(limit_us, _stream_ptr(stream)))
+
+
+TUNE_EXHAUSTIVE, TUNE_ALG2 = 0, 1
+
+
+def hf_autotune(a, b, args, d0=512, mode=TUNE_EXHAUSTIVE, reps=5, flush_l2=False, stream=None):
+    """The (split, regcap, blocks_per_sm) to launch the pair with, by the
+    exhaustive profile or Algorithm 2; returns the timed point as a dict."""
+    best = TunePoint()
+    _check("hf_autotune", lib.hf_autotune(a, b, _argv(args), d0, mode, reps, int(flush_l2),
+                                          _stream_ptr(stream), ctypes.byref(best)))
+    return best.as_dict()

@@ -90,6 +90,27 @@ def test_profile_pair_and_alg2():
     assert splits == sorted(splits)
 
 
+def test_autotune_modes():
+    x, px, coef, (m, v, y, _ws), args = _bn_poly()
+    ka, kb = H.hf_register_kernel(H.BN_STATS), H.hf_register_kernel(H.POLY)
+    ex = H.hf_autotune(ka, kb, args, 256, H.TUNE_EXHAUSTIVE, reps=2)
+    a2 = H.hf_autotune(ka, kb, args, 256, H.TUNE_ALG2, reps=2)
+    for p in (ex, a2):
+        assert p["status"] == 0 and p["time_us"] > 0 and p["split"] % 32 == 0 and 0 < p["split"] < 256
+    assert ex["regcap"] in [0] + H.hf_regcaps()
+    # the exhaustive table contains Algorithm 2's candidates: its pick is no
+    # slower, up to timing noise
+    assert ex["time_us"] <= 1.2 * a2["time_us"]
+    # the returned point launches and computes the same result
+    f = H.hf_fuse(ka, kb, ex["split"], 256, ex["regcap"])
+    H.hf_launch(f, args, ex["grid"])
+    torch.cuda.synchronize()
+    check_poly(px.cpu(), coef, y.cpu())
+    check_bn(x.cpu(), m, v)
+    with pytest.raises(H.HFError):
+        H.hf_autotune(ka, kb, args, 256, 7)
+
+
 def test_calibration_in_plausible_range():
     lim = H.hf_device_info()
     ffma = H.hf_calibrate(H.CAL_FFMA)
