@@ -5,7 +5,7 @@ Here the exhaustive profile of a corpus of generated pairs becomes training
 data for a small perceptron that predicts log(fused time) from static
 features; for a new pair the model scores every candidate with one inference
 launch and the search keeps the predicted best (optionally confirming the
-top few by timing).  The exhaustive search stays the fallback and the judge:
+top few by timing).  The exhaustive search stays the fallback and the yardstick:
 regret = t(model's pick) / t(exhaustive best) - 1, both read from the
 exhaustive table of held-out pairs.
 
