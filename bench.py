@@ -287,6 +287,52 @@ class Ctx:
         return max_over_ranks(v, self.dist, self.dev)
 
 
+def pipelined_e2e(cx, slots, steps, warm=2):
+    """End-to-end time per step with two buffer sets.  Step i copies its
+    inputs from pinned host memory into set i % 2 (one copy stream), runs
+    the launch on them (the compute stream) and copies every output back to
+    pinned host memory (a second copy stream); step i + 1's input copy thus
+    overlaps step i's output copy, the two directions running on separate
+    copy engines.  Events keep a set from being overwritten while step
+    i - 2 still uses it.  slots[b] = (h2d [(host, dev)], d2h [(dev, host)],
+    launch(stream))."""
+    torch = cx.torch
+    s_in, s_k, s_out = (torch.cuda.Stream(device=cx.dev) for _ in range(3))
+    ev_in, ev_k, ev_out = ([torch.cuda.Event() for _ in range(2)] for _ in range(3))
+    used = [False, False]
+
+    def step(i):
+        b = i % 2
+        h2d, d2h, launch = slots[b]
+        if used[b]:
+            s_in.wait_event(ev_k[b])     # step i - 2's launch has read these inputs
+            s_k.wait_event(ev_out[b])    # and its outputs have left
+        with torch.cuda.stream(s_in):
+            for h, d in h2d:
+                d.copy_(h, non_blocking=True)
+        ev_in[b].record(s_in)
+        s_k.wait_event(ev_in[b])
+        launch(s_k)
+        ev_k[b].record(s_k)
+        s_out.wait_event(ev_k[b])
+        with torch.cuda.stream(s_out):
+            for d, h in d2h:
+                h.copy_(d, non_blocking=True)
+        ev_out[b].record(s_out)
+        used[b] = True
+
+    for i in range(warm):
+        step(i)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s_in)
+    for i in range(warm, warm + steps):
+        step(i)
+    e1.record(s_out)   # after the last output copy, which follows every other step's work
+    e1.synchronize()
+    return e0.elapsed_time(e1) * 1e3 / steps
+
+
 def max_over_ranks(value, dist=None, device=None):
     """The slowest rank's time: every rank contributes its own and gets the
     maximum back (one all-reduce; replicas exchange nothing else)."""
@@ -372,16 +418,14 @@ def run_pair(cx, name):
     t_serial = statistics.median(cx.timed(step_serial, max(5, K // 4), warm=Wm, flush=fl))
     t_two = statistics.median(cx.timed(step_two, max(5, K // 4), warm=Wm, flush=fl))
 
-    host_out = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs]
-
-    def step_e2e():
-        for h, d in host_in:
-            d.copy_(h, non_blocking=True)
-        H.hf_launch(fused, args, grid, st)
-        for h, d in zip(host_out, outs):
-            h.copy_(d, non_blocking=True)
-
-    t_e2e = statistics.median(cx.timed(step_e2e, max(3, K // 20), warm=1))
+    # end to end: a second buffer set, inputs in and every output out per step
+    _b2, args2, _n2, _o2, host_in2, outs2 = make_pair(name, H, W, cx.dev)
+    slots = []
+    for a_, hin, outs_ in ((args, host_in, outs), (args2, host_in2, outs2)):
+        hout = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs_]
+        slots.append((hin, list(zip(outs_, hout)),
+                      lambda s_, a_=a_: H.hf_launch(fused, a_, grid, s_)))
+    t_e2e = pipelined_e2e(cx, slots, max(6, K // 20))
     h2d = sum(d.numel() * d.element_size() for _, d in host_in)
     if "hashes" in spec:
         h2d += 80 * len(args)   # the headers travel in the launch's parameter block
@@ -424,7 +468,8 @@ def run_pair(cx, name):
                    "vfuse_us": round(vfuse[0], 3) if vfuse else None,
                    "vfuse_block": vfuse[1] if vfuse else None},
         "roofline": roofline,
-        "e2e": {"value": round(t_e2e, 2), "unit": "us", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": round(t_e2e, 2), "unit": "us", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "mode": "double-buffered: step i+1's inputs copy in while step i's outputs copy out"},
         "gpu_launches": K,
         "clocks": clk.summary(),
     }
@@ -442,26 +487,35 @@ def run_nway(cx):
     from paper_2007_01277_gb300 import workloads as W
     dev, st = cx.dev, cx.stream
     sp = W.WORKLOADS["nway8"]
-    xb = W.bn_input(sp["bn"]).to(dev)
-    mb, vb = torch.empty(sp["bn"][1], device=dev), torch.empty(sp["bn"][1], device=dev)
-    ws = H.bn_stats_workspace(xb)
-    xi = W.im2col_input(sp["im2col"]).to(dev)
-    ci = torch.empty(sp["im2col"][0], sp["im2col"][1] * 9, sp["im2col"][2] * sp["im2col"][3], device=dev)
-    xp = W.maxpool_input(sp["pool"]).to(dev)
-    yp = torch.empty(sp["pool"][:2] + (56, 56), device=dev)
-    xu = W.upsample_input(sp["up"]).to(dev)
-    yu = torch.empty(sp["up"][:2] + (256, 256), device=dev)
-    xh = W.hist_input(sp["hist_n"]).to(dev)
-    bins = torch.zeros(256, dtype=torch.int32, device=dev)
-    po = torch.empty((sp["philox_n"], 4), dtype=torch.int32, device=dev)
-    xq = W.poly_input(sp["poly_n"]).to(dev)
-    yq = torch.empty_like(xq)
-    x16, y16 = (t.to(dev) for t in W.bf16_inputs(sp["bf16_n"]))
-    o16 = torch.empty_like(x16)
+
+    def make_set():
+        """Device tensors and argument blocks of the eight kernels (inputs,
+        outputs and the argument list)."""
+        xb = W.bn_input(sp["bn"]).to(dev)
+        mb, vb = torch.empty(sp["bn"][1], device=dev), torch.empty(sp["bn"][1], device=dev)
+        ws = H.bn_stats_workspace(xb)
+        xi = W.im2col_input(sp["im2col"]).to(dev)
+        ci = torch.empty(sp["im2col"][0], sp["im2col"][1] * 9, sp["im2col"][2] * sp["im2col"][3], device=dev)
+        xp = W.maxpool_input(sp["pool"]).to(dev)
+        yp = torch.empty(sp["pool"][:2] + (56, 56), device=dev)
+        xu = W.upsample_input(sp["up"]).to(dev)
+        yu = torch.empty(sp["up"][:2] + (256, 256), device=dev)
+        xh = W.hist_input(sp["hist_n"]).to(dev)
+        bins = torch.zeros(256, dtype=torch.int32, device=dev)
+        po = torch.empty((sp["philox_n"], 4), dtype=torch.int32, device=dev)
+        xq = W.poly_input(sp["poly_n"]).to(dev)
+        yq = torch.empty_like(xq)
+        x16, y16 = (t.to(dev) for t in W.bf16_inputs(sp["bf16_n"]))
+        o16 = torch.empty_like(x16)
+        a_ = [H.bn_stats_args(xb, mb, vb, ws), H.im2col3_args(xi, ci), H.maxpool3s2_args(xp, yp),
+              H.upsample2x_args(xu, yu), H.hist256_args(xh, bins), H.philox_args(po, 0),
+              H.poly_args(xq, yq, W.poly_coefficients().tolist()), H.bf16_axpy_args(x16, y16, o16)]
+        return [xb, xi, xp, xu, xh, xq, x16, y16], [mb, vb, ci, yp, yu, bins, po, yq, o16], a_
+
+    ins, outs, args = make_set()
+    xb, xi, xp, xu, xh, xq, x16, y16 = ins
+    mb, vb, ci, yp, yu, bins, po, yq, o16 = outs
     bodies = [H.BN_STATS, H.IM2COL3, H.MAXPOOL3S2, H.UPSAMPLE2X, H.HIST256, H.PHILOX, H.POLY, H.BF16_AXPY]
-    args = [H.bn_stats_args(xb, mb, vb, ws), H.im2col3_args(xi, ci), H.maxpool3s2_args(xp, yp),
-            H.upsample2x_args(xu, yu), H.hist256_args(xh, bins), H.philox_args(po, 0),
-            H.poly_args(xq, yq, W.poly_coefficients().tolist()), H.bf16_axpy_args(x16, y16, o16)]
     ks = [H.hf_register_kernel(b) for b in bodies]
     nbytes = sum(t.numel() * t.element_size() for t in (xb, xi, ci, xp, yp, xu, yu, xh, po, xq, yq, x16, y16, o16))
     ops = {"ffma": sp["poly_n"] * 64 * 33, "imul": sp["philox_n"] * 40, "smem_atomic": sp["hist_n"]}
@@ -512,25 +566,29 @@ def run_nway(cx):
     t_serial = statistics.median(cx.timed(lambda: H.hf_graph_launch(graphs["serial"], st), max(5, K // 4), warm=Wm))
     t_nstream = statistics.median(cx.timed(lambda: H.hf_graph_launch(graphs["nstream"], st), max(5, K // 4), warm=Wm))
     t_fused_nograph = statistics.median(cx.timed(issue_fused, max(5, K // 4), warm=Wm))
-    # end to end: every input from pinned host memory, the graph, every output back
-    ins = [xb, xi, xp, xu, xh, xq, x16, y16]
-    outs = [mb, vb, ci, yp, yu, bins, po, yq, o16]
-    host_in = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in ins]
-    for h, d in zip(host_in, ins):
-        h.copy_(d)
-    host_out = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs]
-
-    def step_e2e():
-        for h, d in zip(host_in, ins):
-            d.copy_(h, non_blocking=True)
-        H.hf_graph_launch(graphs["fused"], st)
-        for h, d in zip(host_out, outs):
-            h.copy_(d, non_blocking=True)
-
-    t_e2e = statistics.median(cx.timed(step_e2e, max(3, K // 40), warm=1))
+    # end to end: every input from pinned host memory, the graph, every output
+    # back, with a second buffer set (and its own graph) so that consecutive
+    # steps' copies overlap
+    ins2, outs2, args2 = make_set()
+    with torch.cuda.stream(st):
+        H.hf_launch(fused, args2, grid, st)
+        torch.cuda.synchronize()
+        H.hf_graph_begin(st)
+        H.hf_launch(fused, args2, grid, st)
+        graph2 = H.hf_graph_end(st)
+    slots = []
+    for ins_, outs_, g_ in ((ins, outs, graphs["fused"]), (ins2, outs2, graph2)):
+        hin = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in ins_]
+        for h, d in zip(hin, ins_):
+            h.copy_(d)
+        hout = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs_]
+        slots.append((list(zip(hin, ins_)), list(zip(outs_, hout)),
+                      lambda s_, g_=g_: H.hf_graph_launch(g_, s_)))
+    t_e2e = pipelined_e2e(cx, slots, max(6, K // 40))
     e2e = {"value": round(t_e2e, 2), "unit": "us",
            "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in ins),
-           "d2h_bytes_per_step": sum(t.numel() * t.element_size() for t in outs)}
+           "d2h_bytes_per_step": sum(t.numel() * t.element_size() for t in outs),
+           "mode": "double-buffered: step i+1's inputs copy in while step i's outputs copy out"}
     hbm, peak_kind = measured_peaks()
     peaks = pipe_peaks(H, st)
     t_ideal, terms = ideal_us(nbytes, ops, peaks, hbm)
