@@ -25,6 +25,42 @@ struct BodyPoly {
         return HF_OK;
     }
 
+    // Two floats in one 64-bit register, the operand of the packed FMA.
+    static __device__ __forceinline__ unsigned long long pack2(float a, float b)
+    {
+        unsigned long long r;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+        return r;
+    }
+    static __device__ __forceinline__ void unpack2(unsigned long long r, float &a, float &b)
+    {
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+    }
+
+    // Four chains as two pairs: each packed FMA (fma.rn.f32x2) performs two
+    // independent correctly rounded FMAs, so the results equal the scalar
+    // chains bit for bit with half the instructions -- issue slots are what
+    // the polynomial shares with the other bodies of a fused block.
+    static __device__ __forceinline__ void chain4(float (&v)[4], const float (&c)[HF_POLY_NCOEF],
+                                                  int iters)
+    {
+        unsigned long long A = pack2(0.f, 0.f), B = A;
+        const unsigned long long X = pack2(v[0], v[1]), Y = pack2(v[2], v[3]);
+        unsigned long long c2[HF_POLY_NCOEF];
+#pragma unroll
+        for (int k = 0; k < HF_POLY_NCOEF; ++k) c2[k] = pack2(c[k], c[k]);
+#pragma unroll 1
+        for (int t = 0; t < iters; ++t) {
+#pragma unroll
+            for (int k = HF_POLY_NCOEF - 1; k >= 0; --k) {
+                asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(A) : "l"(X), "l"(c2[k]));
+                asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(B) : "l"(Y), "l"(c2[k]));
+            }
+        }
+        unpack2(A, v[0], v[1]);
+        unpack2(B, v[2], v[3]);
+    }
+
     template <int L>
     static __device__ __forceinline__ void chain(float (&v)[L], const float (&c)[HF_POLY_NCOEF],
                                                  int iters)
@@ -56,7 +92,7 @@ struct BodyPoly {
             for (int64_t i = gt; i < n4; i += stride) {
                 const float4 q = ldcs4(a.x + 4 * i);
                 float v[4] = {q.x, q.y, q.z, q.w};
-                chain<4>(v, c, a.iters);
+                chain4(v, c, a.iters);
                 stcs4(a.y + 4 * i, make_float4(v[0], v[1], v[2], v[3]));
             }
             done = n4 << 2;
