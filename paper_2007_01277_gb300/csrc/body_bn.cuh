@@ -66,6 +66,10 @@ struct BodyBn {
         float p1[VEC], p2[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) p1[v] = 0.f, p2[v] = 0.f;
+        // VEC == 4: the four per-lane sums as two packed pairs (same
+        // operations per value, half the instructions)
+        unsigned long long P1a = f2pack(0.f, 0.f), P1b = P1a, P2a = P1a, P2b = P1a;
+        const unsigned long long KK = f2pack(K, K);
         constexpr int kSteps = kTile / (32 * VEC);
         constexpr int kBatch = 8;
         int64_t j = j0;
@@ -92,14 +96,32 @@ struct BodyBn {
                     ++n;
                 }
             }
+            if (VEC == 4) {
 #pragma unroll
-            for (int b = 0; b < kBatch; ++b)
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) {
-                    float d = __fsub_rn(vals[b][v], K);
-                    p1[v] = __fadd_rn(p1[v], d);
-                    p2[v] = __fmaf_rn(d, d, p2[v]);
+                for (int b = 0; b < kBatch; ++b) {
+                    const unsigned long long Da = f2sub(f2pack(vals[b][0], vals[b][1 % VEC]), KK);
+                    const unsigned long long Db = f2sub(f2pack(vals[b][2 % VEC], vals[b][3 % VEC]), KK);
+                    P1a = f2add(P1a, Da);
+                    P1b = f2add(P1b, Db);
+                    P2a = f2fma(Da, Da, P2a);
+                    P2b = f2fma(Db, Db, P2b);
                 }
+            } else {
+#pragma unroll
+                for (int b = 0; b < kBatch; ++b)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        float d = __fsub_rn(vals[b][v], K);
+                        p1[v] = __fadd_rn(p1[v], d);
+                        p2[v] = __fmaf_rn(d, d, p2[v]);
+                    }
+            }
+        }
+        if (VEC == 4) {
+            f2unpack(P1a, p1[0], p1[1 % VEC]);
+            f2unpack(P1b, p1[2 % VEC], p1[3 % VEC]);
+            f2unpack(P2a, p2[0], p2[1 % VEC]);
+            f2unpack(P2b, p2[2 % VEC], p2[3 % VEC]);
         }
         s1 = p1[0];
         s2 = p2[0];

@@ -25,18 +25,6 @@ struct BodyPoly {
         return HF_OK;
     }
 
-    // Two floats in one 64-bit register, the operand of the packed FMA.
-    static __device__ __forceinline__ unsigned long long pack2(float a, float b)
-    {
-        unsigned long long r;
-        asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-        return r;
-    }
-    static __device__ __forceinline__ void unpack2(unsigned long long r, float &a, float &b)
-    {
-        asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-    }
-
     // Four chains as two pairs: each packed FMA (fma.rn.f32x2) performs two
     // independent correctly rounded FMAs, so the results equal the scalar
     // chains bit for bit with half the instructions -- issue slots are what
@@ -44,21 +32,21 @@ struct BodyPoly {
     static __device__ __forceinline__ void chain4(float (&v)[4], const float (&c)[HF_POLY_NCOEF],
                                                   int iters)
     {
-        unsigned long long A = pack2(0.f, 0.f), B = A;
-        const unsigned long long X = pack2(v[0], v[1]), Y = pack2(v[2], v[3]);
+        unsigned long long A = f2pack(0.f, 0.f), B = A;
+        const unsigned long long X = f2pack(v[0], v[1]), Y = f2pack(v[2], v[3]);
         unsigned long long c2[HF_POLY_NCOEF];
 #pragma unroll
-        for (int k = 0; k < HF_POLY_NCOEF; ++k) c2[k] = pack2(c[k], c[k]);
+        for (int k = 0; k < HF_POLY_NCOEF; ++k) c2[k] = f2pack(c[k], c[k]);
 #pragma unroll 1
         for (int t = 0; t < iters; ++t) {
 #pragma unroll
             for (int k = HF_POLY_NCOEF - 1; k >= 0; --k) {
-                asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(A) : "l"(X), "l"(c2[k]));
-                asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(B) : "l"(Y), "l"(c2[k]));
+                A = f2fma(A, X, c2[k]);
+                B = f2fma(B, Y, c2[k]);
             }
         }
-        unpack2(A, v[0], v[1]);
-        unpack2(B, v[2], v[3]);
+        f2unpack(A, v[0], v[1]);
+        f2unpack(B, v[2], v[3]);
     }
 
     template <int L>
@@ -136,9 +124,12 @@ struct BodyBf16Axpy {
         __nv_bfloat162 h = __floats2bfloat162_rn(u, v);   // .x = u (low half)
         return *reinterpret_cast<unsigned *>(&h);
     }
+    // the two elements of a 32-bit word in one packed FMA
     static __device__ __forceinline__ unsigned axpy2(float al, unsigned x, unsigned y)
     {
-        return pack(__fmaf_rn(al, lo(x), lo(y)), __fmaf_rn(al, hi(x), hi(y)));
+        float r0, r1;
+        f2unpack(f2fma(f2pack(al, al), f2pack(lo(x), hi(x)), f2pack(lo(y), hi(y))), r0, r1);
+        return pack(r0, r1);
     }
 
     static __device__ __forceinline__ uint4 axpy8(float al, uint4 x, uint4 y)

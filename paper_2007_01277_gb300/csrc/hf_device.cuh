@@ -61,6 +61,41 @@ __device__ __forceinline__ void interval_sync(const Ctx &c)
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
+// Packed FP32 pairs: two floats in one 64-bit register and the f32x2
+// operations of sm_100 and later.  Each half is an ordinary correctly
+// rounded operation, so a packed computation equals the scalar one bit for
+// bit; it takes half the instructions (issue slots are what a body shares
+// with the other bodies of a fused block).
+__device__ __forceinline__ unsigned long long f2pack(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2unpack(unsigned long long r, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2add(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // Read-only global loads through the non-coherent path.
 __device__ __forceinline__ float4 ldg4(const float *p)
 {
