@@ -476,6 +476,16 @@ hf_status hf_src_launch_fused(hf_src_module m, void **params_a, void **params_b,
 hf_status hf_src_query(hf_src_module m, int *regs, int *local_bytes, int *static_smem, int *max_threads);
 void hf_src_unload(hf_src_module m);
 
+/* The bulk-copy ring geometry the launch planner gives a block of n
+ * intervals (warps[i] warps; ring[i] != 0 when its kernel can stream
+ * through a ring and wants at least min_bytes[i] in flight per warp) at
+ * blocks_per_sm resident blocks: about 40 KB in flight per SM over the ring
+ * warps, intervals whose minimum the share misses fall back to register
+ * loads (uses[i] = 0), stages of 1, 2 or 4 KB, 2 to 4 per warp; stages = 0
+ * when no interval keeps a ring.  Host arithmetic only. */
+hf_status hf_ring_plan(int n, const int *warps, const int *ring, const unsigned *min_bytes,
+                       int blocks_per_sm, unsigned *stage, int *stages, int *uses);
+
 /* Device-side failure detection.  Bodies that stage their input through
  * bulk asynchronous copies wait on them with a time limit (about 2 s); on
  * expiry the kernel sets a bit in a per-device error word (1 = a bounded

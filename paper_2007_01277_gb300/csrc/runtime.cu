@@ -293,6 +293,31 @@ void ring_geom(double F, unsigned *stage, int *stages)
     *stages = std::min(4, std::max(2, 1 + (int)(F / B + 0.5)));
 }
 
+// The ring decision for `b` resident blocks of a block whose intervals have
+// warps[i] warps, ring[i] (a body that can stream through a ring) and
+// ring_min[i] (the bytes in flight per warp below which it is better off on
+// register loads): intervals whose minimum the SM's share misses drop their
+// ring and the share is recomputed over the rest.  Returns the geometry and
+// which intervals keep a ring.
+void ring_choice(int n, const int *warps, const bool *ring, const unsigned *ring_min, int b, bool *use,
+                 unsigned *stage, int *stages)
+{
+    for (int i = 0; i < n; ++i) use[i] = ring[i] && b > 0;
+    double F = 0.0;
+    for (bool changed = true; changed;) {
+        changed = false;
+        int w = 0;
+        for (int i = 0; i < n; ++i)
+            if (use[i]) w += warps[i];
+        F = w > 0 ? 40960.0 / ((double)b * w) : 0.0;
+        for (int i = 0; i < n; ++i)
+            if (use[i] && F < ring_min[i]) use[i] = false, changed = true;
+    }
+    ring_geom(F, stage, stages);
+    if (*stages == 0)
+        for (int i = 0; i < n; ++i) use[i] = false;
+}
+
 // Shared-memory layout, ring geometry and grid of one launch.
 struct LaunchPlan {
     unsigned off[HF_MAX_INTERVALS];          // slice offsets
@@ -336,20 +361,11 @@ hf_status plan_launch(const void *func, int d0, int n, const int *threads, const
         // share gives drop their ring (register loads), and the share is
         // recomputed over the rest.
         bool use[HF_MAX_INTERVALS];
-        for (int i = 0; i < n; ++i) use[i] = ring[i] && b > 0;
-        double F = 0.0;
-        for (bool changed = true; changed;) {
-            changed = false;
-            int w = 0;
-            for (int i = 0; i < n; ++i)
-                if (use[i]) w += threads[i] / 32;
-            F = w > 0 ? 40960.0 / ((double)b * w) : 0.0;
-            for (int i = 0; i < n; ++i)
-                if (use[i] && F < ring_min[i]) use[i] = false, changed = true;
-        }
+        int warps[HF_MAX_INTERVALS];
+        for (int i = 0; i < n; ++i) warps[i] = threads[i] / 32;
         unsigned stage = 0;
         int stages = 0;
-        ring_geom(F, &stage, &stages);
+        ring_choice(n, warps, ring, ring_min, b, use, &stage, &stages);
         size_t off = 0;
         for (int i = 0; i < n; ++i) {
             out->off[i] = (unsigned)off;
@@ -499,6 +515,19 @@ unsigned *error_word()
 
 // ------------------------------------------------------------------ C ABI
 extern "C" {
+
+hf_status hf_ring_plan(int n, const int *warps, const int *ring, const unsigned *min_bytes,
+                       int blocks_per_sm, unsigned *stage, int *stages, int *uses)
+{
+    if (n < 1 || n > HF_MAX_INTERVALS || !warps || !ring || !min_bytes || !stage || !stages || !uses ||
+        blocks_per_sm < 1)
+        return fail(HF_ERR_INVALID, "bad ring-plan arguments");
+    bool r[HF_MAX_INTERVALS], use[HF_MAX_INTERVALS];
+    for (int i = 0; i < n; ++i) r[i] = ring[i] != 0;
+    ring_choice(n, warps, r, min_bytes, blocks_per_sm, use, stage, stages);
+    for (int i = 0; i < n; ++i) uses[i] = use[i] ? 1 : 0;
+    return HF_OK;
+}
 
 hf_status hf_check_device_error(unsigned *flags, int clear)
 {

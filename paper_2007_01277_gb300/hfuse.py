@@ -180,6 +180,9 @@ def _load():
         "hf_autotune": (_i32, [_P, _P, ctypes.POINTER(_P), _i32, _i32, _i32, _i32, _P,
                                ctypes.POINTER(TunePoint)]),
         "hf_selftest_wait_timeout": (_i32, [_i32, _P]),
+        "hf_ring_plan": (_i32, [_i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_uint),
+                                _i32, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(_i32),
+                                ctypes.POINTER(_i32)]),
         "hf_tmpl_features": (_i32, [ctypes.POINTER(StreamTmplArgs), ctypes.POINTER(StreamTmplArgs),
                                     _i32, _i32, _i32, _i32, _i32, _i32, ctypes.c_double,
                                     ctypes.c_double, ctypes.POINTER(_f32)]),
@@ -617,3 +620,13 @@ def hf_autotune(a, b, args, d0=512, mode=TUNE_EXHAUSTIVE, reps=5, flush_l2=False
     _check("hf_autotune", lib.hf_autotune(a, b, _argv(args), d0, mode, reps, int(flush_l2),
                                           _stream_ptr(stream), ctypes.byref(best)))
     return best.as_dict()
+
+
+def hf_ring_plan(warps, ring, min_bytes, blocks_per_sm):
+    """(stage bytes, stages, [uses]) of the launch planner's ring decision."""
+    n = len(warps)
+    st, ns, uses = ctypes.c_uint(), _i32(), (_i32 * n)()
+    _check("hf_ring_plan", lib.hf_ring_plan(n, (_i32 * n)(*warps), (_i32 * n)(*[int(r) for r in ring]),
+                                            (ctypes.c_uint * n)(*min_bytes), blocks_per_sm,
+                                            ctypes.byref(st), ctypes.byref(ns), uses))
+    return st.value, ns.value, list(uses)

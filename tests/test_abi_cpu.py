@@ -132,3 +132,26 @@ def test_template_features_hand_example(H):
     assert f == pytest.approx(want_a + want_b + want_c, rel=1e-5, abs=1e-7)
     with pytest.raises(H.HFError):
         H.hf_tmpl_features(a, b, 0, 256, 0, 2, 40, 0, 6785.9, 3.8e13)
+
+
+def test_ring_plan_geometry(H):
+    """About 40 KB in flight per SM over the SM's ring warps, in stages of 1,
+    2 or 4 KB, 2 to 4 per warp; below a body's minimum share it drops its
+    ring and the share is recomputed over the rest."""
+    # 8 ring warps: 5 KB per warp -> 4 KB stages, 2 of them
+    assert H.hf_ring_plan([8], [1], [1024], 1) == (4096, 2, [1])
+    # 4 warps: 10 KB per warp -> 4 KB stages, 1 + round(2.5) = 4 (the cap)
+    assert H.hf_ring_plan([4], [1], [1024], 1) == (4096, 4, [1])
+    # 2 warps: 20 KB per warp -> still 4 stages of 4 KB
+    assert H.hf_ring_plan([2], [1], [1024], 1) == (4096, 4, [1])
+    # 32 warps: 1.25 KB -> 1 KB stages, 2 of them
+    assert H.hf_ring_plan([16], [1], [1024], 2) == (1024, 2, [1])
+    # 64 warps: 640 B per warp, below 1 KB -> register loads
+    assert H.hf_ring_plan([16], [1], [1024], 4) == (0, 0, [0])
+    # two ring intervals of 16 warps: 1.25 KB each misses the second one's
+    # 2 KB minimum; it drops out and the first gets 2.5 KB -> 2 KB stages
+    assert H.hf_ring_plan([16, 16], [1, 1], [1024, 2048], 1) == (2048, 2, [1, 0])
+    # intervals without a ring never get one
+    assert H.hf_ring_plan([4, 28], [0, 1], [1024, 1024], 1) == (1024, 2, [0, 1])
+    with pytest.raises(H.HFError):
+        H.hf_ring_plan([4], [1], [1024], 0)
