@@ -83,6 +83,27 @@ def test_upsample(shape, threads, grid):
     check_upsample(x, y)
 
 
+@pytest.mark.parametrize("shape", [(2, 3, 20, 24), (2, 2, 128, 128), (1, 1, 10, 260)])
+def test_upsample_output_alignments(shape):
+    # outputs at byte offsets 0 and 16 take the 128-bit vector path, at 4
+    # the scalar one; all give the same bits and write nothing outside y
+    x = W.upsample_input(shape, seed=3)
+    xd = x.to(DEV)
+    n = x.numel() * 4
+    outs = []
+    for off in (0, 4, 1):
+        buf = torch.full((n + 8,), float("nan"), device=DEV)
+        y = buf[off: off + n].view(shape[:-2] + (2 * shape[-2], 2 * shape[-1]))
+        single(H.UPSAMPLE2X, H.upsample2x_args(xd, y), 256, 7)
+        torch.cuda.synchronize()
+        assert H.hf_check_device_error() == 0
+        check_upsample(x, y)
+        rest = torch.cat([buf[:off], buf[off + n:]])
+        assert torch.isnan(rest).all()   # nothing written outside y
+        outs.append(y.clone())
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
 @pytest.mark.parametrize("shape", [(2, 3, 20, 24), (1, 2, 9, 7), (2, 4, 112, 112), (1, 1, 11, 264),
                                    (1, 1, 1, 1), (2, 1, 2, 4), (3, 2, 37, 36), (1, 3, 57, 128),
                                    (1, 1, 1, 8), (2, 1, 3, 4)])
