@@ -8,13 +8,20 @@ namespace hf {
 
 // ------------------------------------------------------------------------
 // Polynomial chain: acc <- acc * x^33 + p(x), evaluated as one 33-step
-// Horner pass per iteration, `iters` iterations.  Each thread runs four
-// independent elements (one 128-bit group) so every warp has four dependent
-// FMA chains in flight; the coefficients are read once into registers.
+// Horner pass per iteration, `iters` iterations.
+//
+// The work is compute-bound and comes in long, equal units, so its balance
+// across SMs decides the tail.  A unit is 64 consecutive elements (two per
+// lane, advanced together by one packed FMA chain); warps take units in an
+// order that interleaves blocks (warp w of block b has rank w * grid + b),
+// so when the units do not divide evenly the extra ones land on every SM
+// alike instead of on the first blocks.  A warp runs two units at a time
+// (two independent chains per lane) while it has two left.
 struct BodyPoly {
     using Args = hf_poly_args;
     static constexpr int kId = HF_BODY_POLY;
     static constexpr int kBarriers = 0;
+    static constexpr int kUnit = 64;   // elements per warp unit
 
     static __host__ size_t workspace_bytes(const Args &) { return 0; }
     static __host__ size_t smem_bytes(int, const Args &) { return 0; }
@@ -25,46 +32,42 @@ struct BodyPoly {
         return HF_OK;
     }
 
-    // Four chains as two pairs: each packed FMA (fma.rn.f32x2) performs two
-    // independent correctly rounded FMAs, so the results equal the scalar
-    // chains bit for bit with half the instructions -- issue slots are what
-    // the polynomial shares with the other bodies of a fused block.
-    static __device__ __forceinline__ void chain4(float (&v)[4], const float (&c)[HF_POLY_NCOEF],
-                                                  int iters)
+    // One packed FMA (fma.rn.f32x2) performs two independent correctly
+    // rounded FMAs, so each packed chain equals two scalar chains bit for
+    // bit with half the instructions -- issue slots are what the polynomial
+    // shares with the other bodies of a fused block.  NC chains advance
+    // together (NC independent packed FMAs per Horner step).
+    template <int NC>
+    static __device__ __forceinline__ void chains(unsigned long long (&acc)[NC],
+                                                  const unsigned long long (&x)[NC],
+                                                  const float (&c)[HF_POLY_NCOEF], int iters)
     {
-        unsigned long long A = f2pack(0.f, 0.f), B = A;
-        const unsigned long long X = f2pack(v[0], v[1]), Y = f2pack(v[2], v[3]);
-        unsigned long long c2[HF_POLY_NCOEF];
 #pragma unroll
-        for (int k = 0; k < HF_POLY_NCOEF; ++k) c2[k] = f2pack(c[k], c[k]);
+        for (int j = 0; j < NC; ++j) acc[j] = f2pack(0.f, 0.f);
 #pragma unroll 1
         for (int t = 0; t < iters; ++t) {
 #pragma unroll
             for (int k = HF_POLY_NCOEF - 1; k >= 0; --k) {
-                A = f2fma(A, X, c2[k]);
-                B = f2fma(B, Y, c2[k]);
+                const unsigned long long ck = f2pack(c[k], c[k]);
+#pragma unroll
+                for (int j = 0; j < NC; ++j) acc[j] = f2fma(acc[j], x[j], ck);
             }
         }
-        f2unpack(A, v[0], v[1]);
-        f2unpack(B, v[2], v[3]);
     }
 
-    template <int L>
-    static __device__ __forceinline__ void chain(float (&v)[L], const float (&c)[HF_POLY_NCOEF],
-                                                 int iters)
+    // lane's two elements of unit u (zero past the end; never stored)
+    static __device__ __forceinline__ unsigned long long load2(const Args &a, int64_t e)
     {
-        float acc[L], x[L];
-#pragma unroll
-        for (int l = 0; l < L; ++l) x[l] = v[l], acc[l] = 0.f;
-#pragma unroll 1
-        for (int t = 0; t < iters; ++t) {
-#pragma unroll
-            for (int k = HF_POLY_NCOEF - 1; k >= 0; --k)
-#pragma unroll
-                for (int l = 0; l < L; ++l) acc[l] = __fmaf_rn(acc[l], x[l], c[k]);
-        }
-#pragma unroll
-        for (int l = 0; l < L; ++l) v[l] = acc[l];
+        const float v0 = e < a.n ? __ldcs(a.x + e) : 0.f;
+        const float v1 = e + 1 < a.n ? __ldcs(a.x + e + 1) : 0.f;
+        return f2pack(v0, v1);
+    }
+    static __device__ __forceinline__ void store2(const Args &a, int64_t e, unsigned long long r)
+    {
+        float v0, v1;
+        f2unpack(r, v0, v1);
+        if (e < a.n) __stcs(a.y + e, v0);
+        if (e + 1 < a.n) __stcs(a.y + e + 1, v1);
     }
 
     static __device__ void run(const Args &a, const Ctx &cx)
@@ -72,23 +75,24 @@ struct BodyPoly {
         float c[HF_POLY_NCOEF];
 #pragma unroll
         for (int k = 0; k < HF_POLY_NCOEF; ++k) c[k] = a.coef[k];
-        const int64_t gt = (int64_t)cx.block * cx.nthreads + cx.tid;
-        const int64_t stride = (int64_t)cx.grid * cx.nthreads;
-        int64_t done = 0;
-        if (aligned16(a.x) && aligned16(a.y)) {
-            const int64_t n4 = a.n >> 2;
-            for (int64_t i = gt; i < n4; i += stride) {
-                const float4 q = ldcs4(a.x + 4 * i);
-                float v[4] = {q.x, q.y, q.z, q.w};
-                chain4(v, c, a.iters);
-                stcs4(a.y + 4 * i, make_float4(v[0], v[1], v[2], v[3]));
-            }
-            done = n4 << 2;
+        const int64_t units = (a.n + kUnit - 1) / kUnit;
+        const int64_t nwt = (int64_t)cx.grid * (cx.nthreads >> 5);
+        const int64_t lane2 = 2 * lane_id();
+        int64_t u = (int64_t)(cx.tid >> 5) * cx.grid + cx.block;
+        for (; u + nwt < units; u += 2 * nwt) {
+            const int64_t e0 = u * kUnit + lane2, e1 = (u + nwt) * kUnit + lane2;
+            const unsigned long long x[2] = {load2(a, e0), load2(a, e1)};
+            unsigned long long r[2];
+            chains<2>(r, x, c, a.iters);
+            store2(a, e0, r[0]);
+            store2(a, e1, r[1]);
         }
-        for (int64_t i = done + gt; i < a.n; i += stride) {
-            float v[1] = {__ldg(a.x + i)};
-            chain<1>(v, c, a.iters);
-            a.y[i] = v[0];
+        if (u < units) {
+            const int64_t e0 = u * kUnit + lane2;
+            const unsigned long long x[1] = {load2(a, e0)};
+            unsigned long long r[1];
+            chains<1>(r, x, c, a.iters);
+            store2(a, e0, r[0]);
         }
     }
 };
