@@ -4,17 +4,18 @@
 //
 // GB300 layout.  Channel c is the sequence of its M = N*HW values (N runs of
 // HW contiguous floats).  It is cut into tiles of TILE values; one warp
-// reduces one tile at a time (warps stride over all C*T tiles of the grid),
-// streaming it with 128-bit loads, 16 per lane with 8 in flight.  Each tile
+// reduces one tile at a time (each block's warps share its tiles through a
+// counter in shared memory), streaming it with 128-bit loads, 16 per lane
+// with 8 in flight.  Each tile
 // yields FP32 sums of d = x - K_c and d*d, where the shift K_c = x[0][c][0]
 // keeps the variance free of cancellation (the shifted-data algorithm,
 // Chan, Golub & LeVeque 1983).  A warp writes the tile's pair to the
-// workspace; after its last tile it fences and bumps a per-channel counter
-// once per tile, and the warp that brings channel c's counter to T combines
+// workspace and bumps a per-channel counter (an acquire-release atomic),
+// and the warp that brings channel c's counter to T combines
 // that channel's T pairs in FP64 in tile order, writes mean/var and resets
 // the counter.  There is no block barrier in the streaming loop; the
-// reduction order depends only on (tile size, warp), so a fused interval and
-// a standalone launch with the same grid give identical bits.
+// reduction order depends only on the tile size, so a fused interval and a
+// standalone launch give identical bits whatever their threads and grid.
 #pragma once
 #include "hf_device.cuh"
 
@@ -24,14 +25,15 @@ struct BodyBn {
     using Args = hf_bn_stats_args;
     static constexpr int kId = HF_BODY_BN_STATS;
     static constexpr int kTile = 2048;   // values per tile (multiple of 128)
-    static constexpr int kBarriers = 0;
+    static constexpr int kBarriers = 1;   // once, after the tile pool is set up
 
     static __host__ __device__ int64_t tiles_per_channel(const Args &a)
     {
         int64_t M = (int64_t)a.N * a.HW;
         return (M + kTile - 1) / kTile;
     }
-    static __host__ size_t counters_bytes(const Args &a)
+    // Workspace: C per-channel tile counters, then the C*T tile pairs.
+    static __host__ __device__ size_t counters_bytes(const Args &a)
     {
         return ((size_t)a.C * sizeof(unsigned) + 255) / 256 * 256;
     }
@@ -40,7 +42,8 @@ struct BodyBn {
         if (a.C <= 0) return 0;
         return counters_bytes(a) + (size_t)a.C * tiles_per_channel(a) * sizeof(float2);
     }
-    static __host__ size_t smem_bytes(int /*nthreads*/, const Args &) { return 0; }
+    static constexpr size_t kPoolBytes = 16;   // the block's tile pool counter
+    static __host__ size_t smem_bytes(int /*nthreads*/, const Args &) { return kPoolBytes; }
     static __host__ hf_status validate(const Args &a)
     {
         if (a.N < 0 || a.C < 0 || a.HW < 0) return HF_ERR_INVALID;
@@ -139,15 +142,25 @@ struct BodyBn {
 
     // Combine the T tile pairs of channel c (FP64, tile order per lane, then
     // a butterfly whose result is identical on every lane) and write it out.
-    static __device__ __forceinline__ void finalize(const Args &a, int c, int64_t T,
+    // K is the channel's shift; each lane issues its loads four at a time.
+    static __device__ __forceinline__ void finalize(const Args &a, int c, int64_t T, float K,
                                                     const float2 *part, unsigned *cnt)
     {
         const int lane = lane_id();
+        const float2 *pc = part + (int64_t)c * T;
         double s1 = 0.0, s2 = 0.0;
-        for (int64_t t = lane; t < T; t += 32) {
-            float2 q = __ldcg(part + (int64_t)c * T + t);
-            s1 += (double)q.x;
-            s2 += (double)q.y;
+        for (int64_t t0 = 0; t0 < T; t0 += 128) {
+            float2 q[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t t = t0 + 32 * j + lane;
+                q[j] = t < T ? __ldcg(pc + t) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                s1 += (double)q[j].x;
+                s2 += (double)q[j].y;
+            }
         }
 #pragma unroll
         for (int m = 16; m >= 1; m >>= 1) {
@@ -156,68 +169,82 @@ struct BodyBn {
         }
         if (lane == 0) {
             const double M = (double)a.N * (double)a.HW;
-            const double K = (double)__ldg(a.x + (int64_t)c * a.HW);
             const double m1 = s1 / M;
             double var = s2 / M - m1 * m1;
-            a.mean[c] = (float)(K + m1);
+            a.mean[c] = (float)((double)K + m1);
             a.var[c] = (float)(var > 0.0 ? var : 0.0);
             cnt[c] = 0u;
         }
     }
 
+    // Tile assignment.  With the pool (a counter in the interval's shared
+    // memory) block b owns tiles b, b + grid, b + 2 grid, ... and its warps
+    // take them one at a time, asking for the next one a tile ahead: a warp
+    // slowed by a combine, or by the other bodies of a fused block, simply
+    // takes fewer of its block's tiles.  (One dispenser for the whole grid
+    // in global memory serialised every request on one address.)  Without
+    // shared memory, warp w takes tiles w, w + W, ... of the W warps.
     template <int VEC>
-    static __device__ __forceinline__ void run_vec(const Args &a, const Ctx &cx)
+    static __device__ __forceinline__ void run_vec(const Args &a, const Ctx &cx, unsigned *pool)
     {
         const int64_t T = tiles_per_channel(a);
-        const int64_t ntiles = (int64_t)a.C * T;
+        const unsigned long long ntiles = (unsigned long long)a.C * T;
         unsigned *cnt = reinterpret_cast<unsigned *>(a.workspace);
-        float2 *part = reinterpret_cast<float2 *>(
-            reinterpret_cast<unsigned char *>(a.workspace) +
-            ((size_t)a.C * sizeof(unsigned) + 255) / 256 * 256);
-        const int nw = cx.nthreads >> 5;
-        const int64_t gw = (int64_t)cx.block * nw + (cx.tid >> 5);
-        const int64_t TW = (int64_t)cx.grid * nw;
+        float2 *part = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(a.workspace) +
+                                                  counters_bytes(a));
         const int lane = lane_id();
-        int k = 0;
-        for (int64_t tile = gw; tile < ntiles; tile += TW, ++k) {
-            const int c = (int)(tile / T);
-            const int64_t t = tile - (int64_t)c * T;
+        const unsigned long long stride =
+            pool ? (unsigned long long)cx.grid
+                 : (unsigned long long)cx.grid * (unsigned long long)(cx.nthreads >> 5);
+        unsigned long long tile;
+        if (pool) {
+            unsigned i = 0;
+            if (lane == 0) i = atomicAdd(pool, 1u);
+            tile = (unsigned long long)cx.block + stride * __shfl_sync(0xffffffffu, i, 0);
+        } else {
+            tile = (unsigned long long)cx.block * (cx.nthreads >> 5) + (cx.tid >> 5);
+        }
+        while (tile < ntiles) {
+            unsigned inext = 0;
+            if (pool && lane == 0) inext = atomicAdd(pool, 1u);
+            const int c = (int)(tile / (unsigned long long)T);
+            const int64_t t = (int64_t)tile - (int64_t)c * T;
             const float K = __ldg(a.x + (int64_t)c * a.HW);
             float s1, s2;
             tile_sums<VEC>(a, c, t, K, s1, s2);
-            if ((k & 31) == lane) part[tile] = make_float2(s1, s2);
-        }
-        // Release this warp's tile pairs, then count them (lane k%32 wrote
-        // and counts the warp's k-th tile: store -> fence -> atomic in one
-        // thread).
-        __threadfence();
-        k = 0;
-        for (int64_t base = gw; base < ntiles; base += 32 * TW, k += 32) {
-            const int64_t tile = base + (int64_t)lane * TW;
+            // Lane 0 publishes the tile's pair and counts it with an
+            // acquire-release atomic at GPU scope: the release orders the
+            // pair before the count, and the lane whose increment completes
+            // channel c acquires every other warp's pairs of c; the warp
+            // barrier then orders the whole warp's reads after that acquire.
             bool last = false;
-            int c = 0;
-            if (tile < ntiles) {
-                c = (int)(tile / T);
-                last = atomicAdd(cnt + c, 1u) == (unsigned)(T - 1);
+            if (lane == 0) {
+                part[tile] = make_float2(s1, s2);
+                last = atom_add_acq_rel_gpu(cnt + c, 1u) == (unsigned)(T - 1);
             }
-            unsigned mask = __ballot_sync(0xffffffffu, last);
-            if (mask) __threadfence();
-            while (mask) {
-                const int src = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const int cc = __shfl_sync(0xffffffffu, c, src);
-                finalize(a, cc, T, part, cnt);
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __syncwarp();
+                finalize(a, c, T, K, part, cnt);
             }
+            tile = pool ? (unsigned long long)cx.block + stride * __shfl_sync(0xffffffffu, inext, 0)
+                        : tile + stride;
         }
     }
 
     static __device__ void run(const Args &a, const Ctx &cx)
     {
         if (a.C <= 0) return;
+        unsigned *pool = nullptr;
+        if (smem_fits(cx, kPoolBytes)) {
+            pool = reinterpret_cast<unsigned *>(cx.smem);
+            if (cx.tid == 0) *pool = 0u;
+            interval_sync(cx);
+        }
         if ((a.HW & 3) == 0 && aligned16(a.x))
-            run_vec<4>(a, cx);
+            run_vec<4>(a, cx, pool);
         else
-            run_vec<1>(a, cx);
+            run_vec<1>(a, cx, pool);
     }
 };
 

@@ -127,6 +127,16 @@ __device__ __forceinline__ void stcs2(float *p, float2 v)
     __stcs(reinterpret_cast<float2 *>(p), v);
 }
 
+// Atomic add with acquire-release semantics at GPU scope; returns the old
+// value.
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+                 : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 __host__ __device__ __forceinline__ bool aligned16(const void *p)
 {
     return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;

@@ -89,8 +89,7 @@ extern "C" hf_status hf_bn_stats_noalloc(const float *x, float *mean, float *var
     cudaError_t e = cudaMemsetAsync(scratch, 0, BodyBn::counters_bytes(a), st);
     if (e != cudaSuccess) return hf::set_last_error(HF_ERR_CUDA, cudaGetErrorString(e));
 
-    // the body streams its input through a per-warp ring in dynamic shared
-    // memory, sized like every other launch of it
+    // dynamic shared memory as for every other launch of the body
     const size_t smem = BodyBn::smem_bytes(threads, a);
     if (smem > 48 * 1024 &&
         (e = cudaFuncSetAttribute(k_bn_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -59,6 +59,26 @@ def test_bn_bits_independent_of_launch(shape):
         assert torch.equal(m, outs[0][0]) and torch.equal(v, outs[0][1])
 
 
+def test_bn_workspace_counters_rearmed_after_launch():
+    """Every channel's counter is zeroed by its combine, so the counter
+    region is zero after each launch -- also with more blocks than can be
+    resident at once and with blocks that get no tile -- and the bits do
+    not depend on the launch."""
+    x = W.bn_input((4, 6, 40, 40), seed=11).to(DEV)
+    ws = H.bn_stats_workspace(x)
+    ref = None
+    for threads, grid in ((128, 4000), (1024, 1), (32, 700), (256, 0)):
+        m, v = torch.empty(6, device=DEV), torch.empty(6, device=DEV)
+        single(H.BN_STATS, H.bn_stats_args(x, m, v, ws), threads, grid)
+        torch.cuda.synchronize()
+        assert not ws[:256].any(), (threads, grid)   # 6 counters, padded to 256 B
+        if ref is None:
+            ref = (m, v)
+            check_bn(x.cpu(), m, v)
+        assert torch.equal(m, ref[0]) and torch.equal(v, ref[1])
+    assert H.hf_check_device_error() == 0
+
+
 def test_bn_offset_mean_and_constant_channel():
     x = W.bn_input((4, 3, 8, 8)) * 0.01 + 1000.0
     x[:, 1] = 7.25
