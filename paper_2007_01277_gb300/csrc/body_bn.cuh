@@ -12,8 +12,8 @@
 // Chan, Golub & LeVeque 1983).  A warp writes the tile's pair to the
 // workspace and bumps a per-channel counter (an acquire-release atomic),
 // and the warp that brings channel c's counter to T combines
-// that channel's T pairs in FP64 in tile order, writes mean/var and resets
-// the counter.  There is no block barrier in the streaming loop; the
+// that channel's T pairs in tile order (double-float sums), writes mean/var
+// and resets the counter.  There is no block barrier in the streaming loop; the
 // reduction order depends only on the tile size, so a fused interval and a
 // standalone launch give identical bits whatever their threads and grid.
 #pragma once
@@ -140,15 +140,42 @@ struct BodyBn {
         }
     }
 
-    // Combine the T tile pairs of channel c (FP64, tile order per lane, then
-    // a butterfly whose result is identical on every lane) and write it out.
-    // K is the channel's shift; each lane issues its loads four at a time.
+    // Double-float sums: hi + lo, |lo| <= ulp(hi)/2, about 48 significant
+    // bits.  FP64 arithmetic is a narrow, long-latency pipe on this part
+    // (the five-level FP64 butterfly of this combine took 0.45 us, about
+    // 90 ns a level); FP32 adds take a few cycles.  The addition is Knuth's
+    // TwoSum of the high parts (the exact rounding error, whatever the
+    // operand order) plus the low parts, then renormalised; it is
+    // commutative bit for bit, so a butterfly leaves the same value on
+    // every lane.
+    struct DF {
+        float hi, lo;
+    };
+    static __device__ __forceinline__ DF df_add(DF a, DF b)
+    {
+        const float s = __fadd_rn(a.hi, b.hi);
+        const float bb = __fsub_rn(s, a.hi);
+        float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+        e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+        const float hi = __fadd_rn(s, e);
+        return DF{hi, __fsub_rn(e, __fsub_rn(hi, s))};
+    }
+    static __device__ __forceinline__ DF df_shfl_xor(DF a, int m)
+    {
+        return DF{__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
+    }
+
+    // Combine the T tile pairs of channel c (double-float sums, tile order
+    // per lane, then a butterfly whose result is identical on every lane)
+    // and write mean and variance, formed in FP64 by lane 0.  K is the
+    // channel's shift; each lane issues its loads four at a time.
     static __device__ __forceinline__ void finalize(const Args &a, int c, int64_t T, float K,
                                                     const float2 *part, unsigned *cnt)
     {
         const int lane = lane_id();
+        const double inv_m = 1.0 / ((double)a.N * (double)a.HW);   // overlaps the loads
         const float2 *pc = part + (int64_t)c * T;
-        double s1 = 0.0, s2 = 0.0;
+        DF s1{0.f, 0.f}, s2{0.f, 0.f};
         for (int64_t t0 = 0; t0 < T; t0 += 128) {
             float2 q[4];
 #pragma unroll
@@ -158,19 +185,18 @@ struct BodyBn {
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                s1 += (double)q[j].x;
-                s2 += (double)q[j].y;
+                s1 = df_add(s1, DF{q[j].x, 0.f});
+                s2 = df_add(s2, DF{q[j].y, 0.f});
             }
         }
 #pragma unroll
         for (int m = 16; m >= 1; m >>= 1) {
-            s1 += __shfl_xor_sync(0xffffffffu, s1, m);
-            s2 += __shfl_xor_sync(0xffffffffu, s2, m);
+            s1 = df_add(s1, df_shfl_xor(s1, m));
+            s2 = df_add(s2, df_shfl_xor(s2, m));
         }
         if (lane == 0) {
-            const double M = (double)a.N * (double)a.HW;
-            const double m1 = s1 / M;
-            double var = s2 / M - m1 * m1;
+            const double m1 = ((double)s1.hi + (double)s1.lo) * inv_m;
+            const double var = fma(-m1, m1, ((double)s2.hi + (double)s2.lo) * inv_m);
             a.mean[c] = (float)((double)K + m1);
             a.var[c] = (float)(var > 0.0 ? var : 0.0);
             cnt[c] = 0u;
