@@ -60,7 +60,9 @@ def test_autotune_nway_plan_is_valid_and_correct():
     plan, single = H.hf_autotune_nway(ks, args, max_evals=20, reps=2)
     assert len(single) == 4 and all(t > 0 for t in single)
     n_int = plan["n_intervals"]
-    assert 1 <= n_int <= 4 and sum(plan["interval_threads"]) in (512, 1024)
+    # the tuner's seeds use blocks of 512, 768 or 1024 threads
+    assert 1 <= n_int <= 4 and sum(plan["interval_threads"]) in (512, 768, 1024)
+    assert all(t % 32 == 0 and t > 0 for t in plan["interval_threads"])
     assert set(plan["interval_of"]) == set(range(n_int))
     # the seeds (at most 3 block sizes x 5 caps x 2 packings) are always timed
     assert plan["time_us"] > 0 and plan["evals"] <= 20 + 30
