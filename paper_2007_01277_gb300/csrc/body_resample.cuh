@@ -290,9 +290,9 @@ struct BodyMaxpool {
 
 // ------------------------------------------------------------------------
 // im2col, 3x3 window, stride 1, padding 1.  Vector path (W % 4 == 0,
-// W <= 64): a warp takes one (n, c) plane, each half-warp half of its
-// output rows; lane holds 4 columns of three consecutive input rows and
-// writes the nine shifted copies (ky, kx) of its columns for each row.
+// W <= 64): a warp takes a chunk of rows of one (n, c) plane, each half-warp
+// half of the chunk; lane holds 4 columns of three consecutive input rows
+// and writes the nine shifted copies (ky, kx) of its columns for each row.
 struct BodyIm2col {
     using Args = hf_im2col3_args;
     static constexpr int kId = HF_BODY_IM2COL3;
@@ -340,24 +340,35 @@ struct BodyIm2col {
         stcs4(base + 2 * HW, make_float4(r.q.y, r.q.z, r.q.w, r.R));
     }
 
+    // Work items are (plane, chunk of rows); each half-warp takes half of a
+    // chunk.  A plane is cut into as many chunks as give the interval's
+    // warps about three items each (whole planes when there are enough of
+    // them): with one item per plane, 2048 planes kept only 2048 of a
+    // GB300's 9728 warp slots busy.  Every chunk re-reads its two halo rows
+    // (from L2 in practice).
     static __device__ void run_vec(const Args &a, const Ctx &cx)
     {
         const int H = a.H, W = a.W;
         const int64_t HW = (int64_t)H * W;
         const int64_t planes = (int64_t)a.N * a.C;
         const int nw = cx.nthreads >> 5;
+        const int64_t nwt = (int64_t)cx.grid * nw;
         const int lane = lane_id();
         const int half = lane >> 4;
         const int c0 = 4 * (lane & 15);
         const bool act = c0 < W;
-        const int hh = (H + 1) / 2;            // rows per half-warp
-        for (int64_t pl = (int64_t)cx.block * nw + (cx.tid >> 5); pl < planes;
-             pl += (int64_t)cx.grid * nw) {
+        const int want = (int)min((3 * nwt + planes - 1) / planes, (int64_t)(H + 1) / 2);
+        const int hh = ((H + max(want, 1) - 1) / max(want, 1) + 1) / 2;   // rows per half-warp
+        const int nchunk = (H + 2 * hh - 1) / (2 * hh);
+        const int64_t items = planes * nchunk;
+        for (int64_t it = (int64_t)cx.block * nw + (cx.tid >> 5); it < items; it += nwt) {
+            const int64_t pl = it / nchunk;
+            const int ch = (int)(it - pl * nchunk);
             const int64_t n = pl / a.C;
             const int c = (int)(pl - n * a.C);
             const float *xp = a.x + pl * HW;
             float *cp = a.col + (n * a.C * 9 + (int64_t)c * 9) * HW;
-            const int oyb = half * hh;
+            const int oyb = ch * 2 * hh + half * hh;
             const int oye = min(oyb + hh, H);
             Row up = halo(load(xp, oyb - 1, H, W, c0, act), c0, W);
             Row mid = halo(load(xp, oyb, H, W, c0, act), c0, W);
