@@ -11,11 +11,12 @@
  * bodies' (Sec. 2.3).  The thread split and a register bound are chosen by
  * profiling (Algorithm 2, Sec. 3.2).
  *
- * This library does not rewrite CUDA source.  Its kernels are hand-written
- * "bodies" that already address threads through an interval context, so one
- * body serves a standalone launch and any fused interval.  A fused instance
- * is a compiled kernel per (body A, body B, register cap); split, block
- * size, grid and barrier ids are launch-time values.
+ * The built-in kernels are hand-written "bodies" that already address
+ * threads through an interval context, so one body serves a standalone
+ * launch and any fused interval.  A fused instance is a compiled kernel per
+ * (body A, body B, register cap); split, block size, grid and barrier ids
+ * are launch-time values.  Separately, the hf_src_* entry points apply
+ * Algorithm 1 to CUDA source text and compile the result at run time.
  *
  * Conventions for every entry point:
  *   - Pointers named d_* or held in argument blocks are DEVICE pointers the
@@ -79,11 +80,13 @@ typedef enum {
 
 /* Per-channel statistics of x[N][C][HW] (float32): mean[c] and the biased
  * variance var[c] over the N*HW values of channel c.  `workspace` is
- * device scratch of hf_workspace_size() bytes that must be zero-filled
- * before its first use; every completed launch leaves it zero-filled again,
- * so one workspace serves any number of launches on one stream (launches
- * that overlap in time need separate workspaces).  Requires HW % 4 == 0 and
- * x 16-byte aligned for the vector path; other shapes use a scalar path. */
+ * device scratch of hf_workspace_size() bytes (16-byte aligned): C tile
+ * counters, then one partial-sum pair per 2048-value tile.  Zero-fill it
+ * once before its first use; every completed launch leaves the counters at
+ * zero again (the partial sums are written before they are read), so one
+ * workspace serves any number of launches on one stream (launches that
+ * overlap in time need separate workspaces).  Requires HW % 4 == 0 and x
+ * 16-byte aligned for the vector path; other shapes use a scalar path. */
 typedef struct {
     const float *x;
     float *mean;
