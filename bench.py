@@ -422,6 +422,13 @@ def run_pair(cx, name):
     t_fused = cx.max_over_ranks(statistics.mean(per))
     t_serial = statistics.median(cx.timed(step_serial, max(5, K // 4), warm=Wm, flush=fl))
     t_two = statistics.median(cx.timed(step_two, max(5, K // 4), warm=Wm, flush=fl))
+    # the fused launch captured in a CUDA graph (one graph launch per step)
+    H.hf_graph_begin(st)
+    step_fused()
+    g_fused = H.hf_graph_end(st)
+    t_graph = statistics.median(cx.timed(lambda: H.hf_graph_launch(g_fused, st), max(5, K // 4),
+                                         warm=Wm, flush=fl))
+    H.hf_graph_destroy(g_fused)
 
     # end to end: a second buffer set, inputs in and every output out per step
     _b2, args2, _n2, _o2, host_in2, outs2 = make_pair(name, H, W, cx.dev)
@@ -466,6 +473,7 @@ def run_pair(cx, name):
                          "inputs larger than L2 (%.0f MB touched per step)" % _mb(nbytes),
                    "parallelism": "replicas" if cx.world > 1 else "single"},
         "serial_us": round(t_serial, 3), "two_stream_us": round(t_two, 3),
+        "fused_graph_us": round(t_graph, 3),
         "standalone_us": {H.BODY_NAMES[bodies[0]]: round(ta, 3), H.BODY_NAMES[bodies[1]]: round(tb, 3),
                           "threads": [thr_a, thr_b]},
         "speedup_vs_best_native": round(min(t_serial, t_two) / t_fused, 4),
