@@ -235,6 +235,13 @@ def pipe_peaks(H, stream):
             "ialu": H.hf_calibrate(H.CAL_IALU, stream)}
 
 
+def spread(per):
+    """Median and 10th / 90th percentiles of the per-step times (us)."""
+    q = sorted(per)
+    pick = lambda f: q[min(int(f * (len(q) - 1) + 0.5), len(q) - 1)]
+    return {"median": round(pick(0.5), 3), "p10": round(pick(0.1), 3), "p90": round(pick(0.9), 3)}
+
+
 def ideal_us(nbytes, ops, peaks, hbm_gbs):
     terms = {"hbm": nbytes / (hbm_gbs * 1e9) * 1e6}
     for k, v in ops.items():
@@ -473,7 +480,7 @@ def run_pair(cx, name):
                          "inputs larger than L2 (%.0f MB touched per step)" % _mb(nbytes),
                    "parallelism": "replicas" if cx.world > 1 else "single"},
         "serial_us": round(t_serial, 3), "two_stream_us": round(t_two, 3),
-        "fused_graph_us": round(t_graph, 3),
+        "fused_graph_us": round(t_graph, 3), "fused_spread_us": spread(per),
         "standalone_us": {H.BODY_NAMES[bodies[0]]: round(ta, 3), H.BODY_NAMES[bodies[1]]: round(tb, 3),
                           "threads": [thr_a, thr_b]},
         "speedup_vs_best_native": round(min(t_serial, t_two) / t_fused, 4),
@@ -620,7 +627,7 @@ def run_nway(cx):
         "config": {"workload": NWAY_DESC, "plan": plan, "l2": "inputs larger than L2 (%.0f MB per step)" % _mb(nbytes),
                    "parallelism": "replicas" if cx.world > 1 else "single"},
         "serial_us": round(t_serial, 3), "n_stream_us": round(t_nstream, 3),
-        "fused_no_graph_us": round(t_fused_nograph, 3),
+        "fused_no_graph_us": round(t_fused_nograph, 3), "fused_spread_us": spread(per),
         "standalone_us": {H.BODY_NAMES[b]: round(t, 2) for b, t in zip(bodies, single)},
         "speedup_vs_best_native": round(min(t_serial, t_nstream) / t_fused, 4),
         "ideal_us": round(t_ideal, 3), "ideal_terms_us": terms, "frac_of_ideal": round(t_ideal / t_fused, 4),
