@@ -4,9 +4,9 @@
 //
 // GB300 layout.  Channel c is the sequence of its M = N*HW values (N runs of
 // HW contiguous floats).  It is cut into tiles of TILE values; one warp
-// reduces one tile at a time (each block's warps share its tiles through a
-// counter in shared memory), streaming it with 128-bit loads, 16 per lane
-// with 8 in flight.  Each tile
+// reduces one tile at a time (each block's warps share its contiguous range
+// of tiles through a counter in shared memory), streaming it with 128-bit
+// loads, 16 per lane with 8 in flight.  Each tile
 // yields FP32 sums of d = x - K_c and d*d, where the shift K_c = x[0][c][0]
 // keeps the variance free of cancellation (the shifted-data algorithm,
 // Chan, Golub & LeVeque 1983).  A warp writes the tile's pair to the
@@ -204,12 +204,16 @@ struct BodyBn {
     }
 
     // Tile assignment.  With the pool (a counter in the interval's shared
-    // memory) block b owns tiles b, b + grid, b + 2 grid, ... and its warps
-    // take them one at a time, asking for the next one a tile ahead: a warp
-    // slowed by a combine, or by the other bodies of a fused block, simply
-    // takes fewer of its block's tiles.  (One dispenser for the whole grid
-    // in global memory serialised every request on one address.)  Without
-    // shared memory, warp w takes tiles w, w + W, ... of the W warps.
+    // memory) block b owns a contiguous range of about C*T/grid tiles and
+    // its warps take them in order one at a time, asking for the next one a
+    // tile ahead: a warp slowed by a combine, or by the other bodies of a
+    // fused block, simply takes fewer of its block's tiles.  A channel's
+    // tiles then belong to a few neighbouring blocks, completed one after
+    // another (64x256x56x56: 40.9 us against 44.9 with tiles b, b + grid,
+    // ..., which spread each channel over 98 blocks finishing together).
+    // One dispenser for the whole grid in global memory serialised every
+    // request on one address.  Without shared memory, warp w takes tiles
+    // w, w + W, ... of the W warps.
     template <int VEC>
     static __device__ __forceinline__ void run_vec(const Args &a, const Ctx &cx, unsigned *pool)
     {
@@ -219,14 +223,19 @@ struct BodyBn {
         float2 *part = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(a.workspace) +
                                                   counters_bytes(a));
         const int lane = lane_id();
-        const unsigned long long stride =
-            pool ? (unsigned long long)cx.grid
-                 : (unsigned long long)cx.grid * (unsigned long long)(cx.nthreads >> 5);
+        const unsigned long long stride = (unsigned long long)cx.grid * (unsigned long long)(cx.nthreads >> 5);
+        // block b's range [bstart, bend): the first ntiles % grid blocks get
+        // one tile more
+        const unsigned long long G = (unsigned long long)cx.grid, b = (unsigned long long)cx.block;
+        const unsigned long long q = ntiles / G, rem = ntiles % G;
+        const unsigned long long bstart = b * q + (b < rem ? b : rem);
+        const unsigned long long bend = bstart + q + (b < rem ? 1ull : 0ull);
         unsigned long long tile;
         if (pool) {
             unsigned i = 0;
             if (lane == 0) i = atomicAdd(pool, 1u);
-            tile = (unsigned long long)cx.block + stride * __shfl_sync(0xffffffffu, i, 0);
+            tile = bstart + __shfl_sync(0xffffffffu, i, 0);
+            if (tile >= bend) tile = ntiles;
         } else {
             tile = (unsigned long long)cx.block * (cx.nthreads >> 5) + (cx.tid >> 5);
         }
@@ -253,8 +262,12 @@ struct BodyBn {
                 __syncwarp();
                 finalize(a, c, T, K, part, cnt);
             }
-            tile = pool ? (unsigned long long)cx.block + stride * __shfl_sync(0xffffffffu, inext, 0)
-                        : tile + stride;
+            if (pool) {
+                tile = bstart + __shfl_sync(0xffffffffu, inext, 0);
+                if (tile >= bend) tile = ntiles;
+            } else {
+                tile += stride;
+            }
         }
     }
 
