@@ -242,6 +242,21 @@ def spread(per):
     return {"median": round(pick(0.5), 3), "p10": round(pick(0.1), 3), "p90": round(pick(0.9), 3)}
 
 
+def dominant_roofline(terms, nbytes, ops, peaks, t_us, hbm_gbs, peak_kind, traffic):
+    """The roofline of the term that bounds the ideal: HBM bytes, or the
+    operations of the busiest pipe against its calibrated rate."""
+    dom = max(terms, key=terms.get)
+    if dom != "hbm":
+        achieved = ops[dom] / (t_us * 1e-6) / 1e12
+        return {"bound": "alu", "pipe": dom, "achieved": round(achieved, 3),
+                "peak": round(peaks[dom] / 1e12, 3), "unit": "Tops/s",
+                "frac": round(achieved * 1e12 / peaks[dom], 4), "traffic": traffic,
+                "peak_source": "measured in this run: %s (calibration kernel)" % PIPE_DESC[dom]}
+    achieved = nbytes / (t_us * 1e-6) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_gbs, "unit": "GB/s",
+            "frac": round(achieved / hbm_gbs, 4), "traffic": traffic, "peak_source": peak_kind}
+
+
 def ideal_us(nbytes, ops, peaks, hbm_gbs):
     terms = {"hbm": nbytes / (hbm_gbs * 1e9) * 1e6}
     for k, v in ops.items():
@@ -453,21 +468,8 @@ def run_pair(cx, name):
     hbm, peak_kind = measured_peaks()
     peaks = pipe_peaks(H, st)
     t_ideal, terms = ideal_us(nbytes, ops, peaks, hbm)
-    # the roofline of the term that bounds the ideal: HBM bytes, or the ops
-    # of the busiest pipe against its calibrated rate
-    dom = max(terms, key=terms.get)
-    if dom != "hbm":
-        achieved = ops[dom] / (t_fused * 1e-6) / 1e12
-        roofline = {"bound": "alu", "pipe": dom, "achieved": round(achieved, 3),
-                    "peak": round(peaks[dom] / 1e12, 3), "unit": "Tops/s",
-                    "frac": round(achieved * 1e12 / peaks[dom], 4),
-                    "traffic": load_traffic(spec["name"]),
-                    "peak_source": "measured in this run: %s (calibration kernel)" % PIPE_DESC[dom]}
-    else:
-        achieved = nbytes / (t_fused * 1e-6) / 1e9
-        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                    "frac": round(achieved / hbm, 4), "traffic": load_traffic(spec["name"]),
-                    "peak_source": peak_kind}
+    roofline = dominant_roofline(terms, nbytes, ops, peaks, t_fused, hbm, peak_kind,
+                                 load_traffic(spec["name"]))
     info = H.hf_query(fused, args)
     return {
         "metric": METRIC, "value": round(t_fused, 3), "unit": "us",
@@ -616,7 +618,6 @@ def run_nway(cx):
     hbm, peak_kind = measured_peaks()
     peaks = pipe_peaks(H, st)
     t_ideal, terms = ideal_us(nbytes, ops, peaks, hbm)
-    achieved = nbytes / (t_fused * 1e-6) / 1e9
     for g in graphs.values():
         H.hf_graph_destroy(g)
     return {
@@ -632,9 +633,8 @@ def run_nway(cx):
         "speedup_vs_best_native": round(min(t_serial, t_nstream) / t_fused, 4),
         "ideal_us": round(t_ideal, 3), "ideal_terms_us": terms, "frac_of_ideal": round(t_ideal / t_fused, 4),
         "pipe_peaks_per_s": {k: float("%.4g" % v) for k, v in peaks.items()},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4), "traffic": load_traffic("nway8"),
-                     "peak_source": peak_kind},
+        "roofline": dominant_roofline(terms, nbytes, ops, peaks, t_fused, hbm, peak_kind,
+                                      load_traffic("nway8")),
         "e2e": e2e, "gpu_launches": K, "clocks": clk.summary(),
     }
 
