@@ -506,7 +506,8 @@ hf_status hf_selftest_wait_timeout(int limit_us, void *stream);
 /* Measured throughput of one execution pipe on the current device, for
  * the compute terms of the ideal-overlap bound: what = 0 FP32 fused
  * multiply-adds per second, 1 32-bit integer multiplies (high or low half)
- * per second, 2 shared-memory atomic adds per second (conflict-free),
+ * per second as the Philox4x32 round issues them (four per round, with its
+ * XORs), 2 shared-memory atomic adds per second (conflict-free),
  * 3 32-bit integer ALU operations per second in the add / XOR / rotate mix
  * of the hash rounds.
  * Runs a few milliseconds of calibration kernels on `stream`. */
