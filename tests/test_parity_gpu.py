@@ -152,6 +152,22 @@ def test_im2col(shape, threads, grid):
     assert np.array_equal(col.cpu().numpy(), oracle.im2col3(x.numpy()))
 
 
+@pytest.mark.parametrize("shape", [(2, 4, 56, 56), (1, 3, 57, 60), (3, 2, 7, 64)])
+def test_im2col_row_chunks(shape):
+    # the grid decides how many row chunks a plane is cut into (whole planes
+    # for a single warp, down to one row per half-warp for many): every
+    # chunking writes every element exactly once, bit-exact
+    x = W.im2col_input(shape, seed=sum(shape) + 1)
+    xd = x.to(DEV)
+    N, C, H_, W_ = shape
+    ref = oracle.im2col3(x.numpy())
+    for threads, grid in ((32, 1), (64, 40), (256, 0), (768, 3)):
+        col = torch.full((N, C * 9, H_ * W_), float("nan"), device=DEV)
+        single(H.IM2COL3, H.im2col3_args(xd, col), threads, grid)
+        torch.cuda.synchronize()
+        assert np.array_equal(col.cpu().numpy(), ref), (threads, grid)
+
+
 @pytest.mark.parametrize("n,offset", [(0, 0), (1, 0), (15, 0), (16, 0), (17, 0), (1000003, 0),
                                       (100000, 1), (5 << 20, 0)])
 @pytest.mark.parametrize("threads,grid", [(256, 0), (128, 3), (1024, 5)])
@@ -188,6 +204,27 @@ def test_poly(n, offset, iters, threads, grid):
     single(H.POLY, H.poly_args(xd, y, coef, iters), threads, grid)
     torch.cuda.synchronize()
     check_poly(x[offset:], coef, y, iters)
+
+
+@pytest.mark.parametrize("n", [63, 64, 65, 130, 64 * 37 + 5])
+def test_poly_units_bits_independent_of_launch(n):
+    """64-element warp units in a block-interleaved order: every element is
+    computed exactly once whatever the grid (more warps than units, fewer,
+    uneven counts, a partial last unit), with the same bits."""
+    x = W.poly_input(n + 2, seed=n)
+    coef = W.poly_coefficients().numpy()
+    xd = x.to(DEV)
+    ref = None
+    for threads, grid in ((32, 1), (96, 7), (1024, 152), (64, 300), (256, 0)):
+        buf = torch.full((n + 2,), float("nan"), device=DEV)
+        single(H.POLY, H.poly_args(xd[1: n + 1], buf[1: n + 1], coef, 8), threads, grid)
+        torch.cuda.synchronize()
+        assert torch.isnan(buf[0]) and torch.isnan(buf[n + 1])   # nothing outside y
+        y = buf[1: n + 1].clone()
+        if ref is None:
+            ref = y
+            check_poly(x[1: n + 1], coef, y, 8)
+        assert torch.equal(y, ref), (threads, grid)
 
 
 @pytest.mark.parametrize("n,offset", [(1, 0), (9, 0), (100003, 0), (4096, 1), ((1 << 21) + 40, 0)])
