@@ -492,8 +492,9 @@ hf_status hf_ring_plan(int n, const int *warps, const int *ring, const unsigned 
 /* Device-side failure detection.  Bodies that stage their input through
  * bulk asynchronous copies wait on them with a time limit (about 2 s); on
  * expiry the kernel sets a bit in a per-device error word (1 = a bounded
- * wait expired), waits (bounded) for its copies in flight and stops
- * consuming, so the context stays usable and the host can detect it.
+ * wait on bulk copies expired, 2 = a bounded software barrier expired),
+ * waits (bounded) for its copies in flight and stops consuming, so the
+ * context stays usable and the host can detect it.
  * hf_check_device_error reads the word after the launches have finished
  * (synchronize the streams first) and clears it when `clear` is set. */
 hf_status hf_check_device_error(unsigned *flags, int clear);
@@ -502,6 +503,18 @@ hf_status hf_check_device_error(unsigned *flags, int clear);
  * limit of limit_us microseconds (1 .. 10^7): it must give up and set bit
  * 1 of the error word.  Tests the timeout path without any fault. */
 hf_status hf_selftest_wait_timeout(int limit_us, void *stream);
+
+/* Barrier-schedule check without the risk of a hang (Sec. 3.1's partial
+ * barriers wait for a count of threads; a count that is never reached would
+ * stall a hardware barrier for good).  Launches one block of `warps` warps
+ * (1..32) that run `rounds` (1..1000) rounds of a software barrier over all
+ * of them with a wait bounded by limit_us microseconds (1 .. 10^7); warp
+ * `missing` (or none when -1) skips the barrier.  Each warp adds the rounds
+ * it completed to *d_completed (device pointer, may be NULL).  With every
+ * warp present all rounds complete; with one missing the others give up,
+ * set bit 2 of the error word and leave the context usable. */
+hf_status hf_selftest_barrier(int warps, int missing, int rounds, int limit_us,
+                              unsigned *d_completed, void *stream);
 
 /* Measured throughput of one execution pipe on the current device, for
  * the compute terms of the ideal-overlap bound: what = 0 FP32 fused

@@ -106,6 +106,26 @@ __global__ void k_cal_satom(unsigned *out, int iters)
 // A bounded wait that nothing completes: one warp waits on an mbarrier no
 // copy will ever arrive at, gives up after limit_ns and records
 // kErrWaitExpired.  No copy is in flight, so giving up is safe.
+// Rounds of the bounded software barrier over every warp of the block but
+// `missing` (-1: none).  With every warp present each round completes; with
+// one missing the others give up after limit_ns and set kErrBarrierExpired.
+// No warp waits on anything another block owns.
+__global__ void k_selftest_barrier(unsigned *err, int missing, int rounds, unsigned long long limit_ns,
+                                   unsigned *completed)
+{
+    __shared__ unsigned bar[2];
+    if (threadIdx.x == 0) bar[0] = bar[1] = 0u;
+    __syncthreads();
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (w == missing) return;
+    int done = 0;
+    for (int r = 0; r < rounds; ++r) {
+        if (!hf::soft_barrier(bar, nw, err, limit_ns)) break;
+        ++done;
+    }
+    if ((threadIdx.x & 31) == 0 && completed) atomicAdd(completed, (unsigned)done);
+}
+
 __global__ void k_selftest_wait(unsigned *err, unsigned long long limit_ns)
 {
     extern __shared__ __align__(128) unsigned char sm[];
@@ -180,6 +200,19 @@ extern "C" hf_status hf_calibrate(int what, void *stream, double *ops_per_s)
         *ops_per_s = (double)blocks * threads * (iters / 4) * 8 / (ms * 1e-3);
     }
     if (st) return hf::set_last_error(st, "calibration kernel failed");
+    return HF_OK;
+}
+
+extern "C" hf_status hf_selftest_barrier(int warps, int missing, int rounds, int limit_us,
+                                         unsigned *d_completed, void *stream)
+{
+    if (warps < 1 || warps > 32 || missing < -1 || missing >= warps || rounds < 1 || rounds > 1000)
+        return hf::set_last_error(HF_ERR_INVALID, "bad self-test shape");
+    if (limit_us <= 0 || limit_us > 10000000) return hf::set_last_error(HF_ERR_INVALID, "limit out of range");
+    k_selftest_barrier<<<1, 32 * warps, 0, static_cast<cudaStream_t>(stream)>>>(
+        hf::error_word(), missing, rounds, 1000ull * limit_us, d_completed);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return hf::set_last_error(HF_ERR_CUDA, cudaGetErrorString(e));
     return HF_OK;
 }
 

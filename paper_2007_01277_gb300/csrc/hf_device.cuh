@@ -31,7 +31,8 @@ struct Ctx {
 };
 
 // Bits of the device error word read by hf_check_device_error().
-constexpr unsigned kErrWaitExpired = 1u;   // a bounded wait on a bulk copy gave up
+constexpr unsigned kErrWaitExpired = 1u;      // a bounded wait on a bulk copy gave up
+constexpr unsigned kErrBarrierExpired = 2u;   // a bounded software barrier gave up
 
 // Shared-space address of the start of dynamic shared memory plus its size
 // as launched (the %dynamic_smem_size register).
@@ -60,6 +61,47 @@ __device__ __forceinline__ void interval_sync(const Ctx &c)
 }
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ unsigned long long timer_ns();
+
+// A software barrier over `nwarps` warps with a bounded wait, for checking a
+// barrier schedule without the risk of a hang: where a hardware barrier
+// whose count is never reached would stall its warps for good, this one
+// gives up after limit_ns of the global timer, sets kErrBarrierExpired in
+// the error word and returns false.  bar points to two shared words
+// (arrivals, generation), zero before first use; lane 0 of each warp
+// arrives once, the last arrival resets the count and advances the
+// generation, the others wait for the generation to change.
+__device__ __forceinline__ bool soft_barrier(unsigned *bar, int nwarps, unsigned *err,
+                                             unsigned long long limit_ns)
+{
+    volatile unsigned *vb = bar;
+    bool ok = true;
+    __syncwarp();
+    if (lane_id() == 0) {
+        const unsigned gen = vb[1];
+        __threadfence_block();
+        if (atomicAdd(&bar[0], 1u) + 1u == (unsigned)nwarps) {
+            vb[0] = 0u;
+            __threadfence_block();
+            atomicAdd(&bar[1], 1u);
+        } else {
+            const unsigned long long t0 = timer_ns();
+            while (vb[1] == gen) {
+                if (timer_ns() - t0 > limit_ns) {
+                    if (err) atomicOr(err, kErrBarrierExpired);
+                    ok = false;
+                    break;
+                }
+                __nanosleep(64);
+            }
+            __threadfence_block();
+        }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    return ok;
+}
 
 // Packed FP32 pairs: two floats in one 64-bit register and the f32x2
 // operations of sm_100 and later.  Each half is an ordinary correctly

@@ -180,6 +180,7 @@ def _load():
         "hf_autotune": (_i32, [_P, _P, ctypes.POINTER(_P), _i32, _i32, _i32, _i32, _P,
                                ctypes.POINTER(TunePoint)]),
         "hf_selftest_wait_timeout": (_i32, [_i32, _P]),
+        "hf_selftest_barrier": (_i32, [_i32, _i32, _i32, _i32, _P, _P]),
         "hf_ring_plan": (_i32, [_i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_uint),
                                 _i32, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(_i32),
                                 ctypes.POINTER(_i32)]),
@@ -597,6 +598,7 @@ def hf_src_unload(m):
 
 # ----------------------------------------------------------------- device errors
 ERR_WAIT_EXPIRED = 1
+ERR_BARRIER_EXPIRED = 2
 
 
 def hf_check_device_error(clear=False):
@@ -608,6 +610,13 @@ def hf_check_device_error(clear=False):
 
 def hf_selftest_wait_timeout(limit_us, stream=None):
     _check("hf_selftest_wait_timeout", lib.hf_selftest_wait_timeout(limit_us, _stream_ptr(stream)))
+
+
+def hf_selftest_barrier(warps, missing, rounds, limit_us, completed=None, stream=None):
+    """completed: an int32 device tensor of one element (or None)."""
+    ptr = _ptr(completed) if completed is not None else None
+    _check("hf_selftest_barrier", lib.hf_selftest_barrier(warps, missing, rounds, limit_us, ptr,
+                                                          _stream_ptr(stream)))
 
 
 TUNE_EXHAUSTIVE, TUNE_ALG2 = 0, 1

@@ -156,3 +156,35 @@ def test_bounded_wait_expires_and_sets_the_error_word():
     assert float(x.sum().item()) == 1023 * 1024 / 2
     with pytest.raises(H.HFError):
         H.hf_selftest_wait_timeout(0)
+
+
+@pytest.mark.parametrize("warps", [1, 4, 32])
+def test_soft_barrier_completes_with_every_warp(warps):
+    """The bounded software barrier: every round completes when all warps
+    arrive, and no error is reported."""
+    torch.cuda.synchronize()
+    H.hf_check_device_error(clear=True)
+    done = torch.zeros(1, dtype=torch.int32, device="cuda")
+    H.hf_selftest_barrier(warps, -1, 50, 500000, done)
+    torch.cuda.synchronize()
+    assert int(done.item()) == 50 * warps
+    assert H.hf_check_device_error() == 0
+
+
+def test_soft_barrier_gives_up_on_a_missing_warp():
+    """A barrier count that is never reached (one warp skips it) ends in a
+    bounded time with bit 2 of the error word instead of a hang; the context
+    stays usable."""
+    torch.cuda.synchronize()
+    H.hf_check_device_error(clear=True)
+    done = torch.zeros(1, dtype=torch.int32, device="cuda")
+    H.hf_selftest_barrier(8, 3, 5, 2000, done)
+    torch.cuda.synchronize()
+    assert int(done.item()) == 0
+    assert H.hf_check_device_error(clear=True) & H.ERR_BARRIER_EXPIRED
+    assert H.hf_check_device_error() == 0
+    x = torch.arange(1024, dtype=torch.float32, device="cuda")
+    assert float(x.sum().item()) == 1023 * 1024 / 2
+    for bad in ((0, -1, 1, 10), (33, -1, 1, 10), (4, 4, 1, 10), (4, -1, 0, 10), (4, -1, 1, 0)):
+        with pytest.raises(H.HFError):
+            H.hf_selftest_barrier(*bad)
