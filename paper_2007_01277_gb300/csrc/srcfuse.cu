@@ -14,9 +14,10 @@
 //     second (the warp-uniform branch of Algorithm 1).
 // blockIdx and gridDim pass through unchanged.  Rejected (HF_ERR_UNSUPPORTED):
 // threadIdx/blockDim .y/.z, the counting barrier variants, kernel
-// templates, file-scope extern __shared__ arrays, and block-level builtins
+// templates, file-scope extern __shared__ arrays, block-level builtins
 // used outside a kernel body (in a __device__ helper the rewriter would
-// have to thread the context through).
+// have to thread the context through) and in preprocessor lines (a macro
+// would carry them into the fused kernel unrewritten).
 //
 // NVRTC is loaded on first use (dlopen), and the module-loading / launch
 // calls of the driver API are resolved through the runtime's driver entry
@@ -250,6 +251,22 @@ bool builtin(const std::string &x)
     return x == "threadIdx" || x == "blockDim" || x.compare(0, 13, "__syncthreads") == 0;
 }
 
+// True when a preprocessor line names a block-level builtin: a macro would
+// carry it past the rewriter into the fused kernel unchanged.
+bool pp_builtin(const std::string &line)
+{
+    for (size_t i = 0; i < line.size();) {
+        if (is_id0(line[i])) {
+            const size_t b = i;
+            while (i < line.size() && is_id(line[i])) ++i;
+            if (builtin(line.substr(b, i - b))) return true;
+        } else {
+            ++i;
+        }
+    }
+    return false;
+}
+
 // Rewrites one kernel into an interval body; appends the new text of tokens
 // [k.head, k.rbrace] to `out`.
 bool rewrite_kernel(const std::vector<Tok> &t, const Kernel &k, std::string &out, std::string &why)
@@ -340,6 +357,11 @@ bool rewrite_source(const std::string &src, const std::vector<std::string> &name
             if (i > k.lbrace && i < k.rbrace) inside = true;
         if (!inside && t[i].kind == Tok::Ident && builtin(t[i].text)) {
             why = t[i].text + " outside a kernel body (a __device__ helper): inline it into the kernel";
+            return false;
+        }
+        if (t[i].kind == Tok::PP && pp_builtin(t[i].text)) {
+            why = "a preprocessor line names threadIdx, blockDim or __syncthreads (a macro is not "
+                  "rewritten): expand it in the kernel";
             return false;
         }
         if (!inside && is(t, i, "extern") && is(t, i + 1, "__shared__")) {

@@ -98,12 +98,36 @@ def test_fused_source_compiles_with_nvrtc():
     ("__device__ int tid() { return threadIdx.x; }\n__global__ void k(int *p) { p[tid()] = 0; }", "outside"),
     ("extern __shared__ float s[];\n__global__ void k(float *p) { p[0] = s[0]; }", "file-scope"),
     ("template <int N> __global__ void k(int *p) { p[0] = N; }", "templates"),
+    ("#define TID threadIdx.x\n__global__ void k(int *p) { p[TID] = 0; }", "preprocessor"),
+    ("#define SYNC() __syncthreads()\n__global__ void k(int *p) { SYNC(); p[0] = 0; }", "preprocessor"),
 ])
 def test_unsupported_forms_are_rejected(src, why):
     with pytest.raises(H.HFError) as e:
         H.hf_src_fuse(src, "k", SRC, "byte_hist", 64, 128)
     assert e.value.status == -6
     assert why in str(e.value)
+
+
+def test_comments_strings_and_pragmas_pass_through():
+    # builtins named in comments or string literals are not code; pragmas and
+    # macros without builtins are kept as they are
+    src = r'''
+#define SCALE 2.0f
+// threadIdx.x in a comment, __syncthreads() too
+__global__ void k(float *p, int n)
+{
+    const char *tag = "blockDim.x"; (void)tag;   /* threadIdx */
+#pragma unroll 4
+    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] *= SCALE;
+    __syncthreads();
+}
+'''
+    out = H.hf_src_fuse(src, "k", SRC, "byte_hist", 64, 128)
+    body = out[: out.index("hf_src_fused(")]
+    assert "// threadIdx.x in a comment, __syncthreads() too" in body
+    assert '"blockDim.x"' in body and "#pragma unroll 4" in body and "#define SCALE 2.0f" in body
+    assert "i = hf_tid_" in body and "i += hf_ntid_" in body
+    H.hf_src_compile_check(out, "hf_src_fused")
 
 
 def test_bad_names_and_splits():
