@@ -1,15 +1,21 @@
 """Benchmark of the horizontally fused hot path on one GB300.
 
-Default workload: the memory+memory pair -- bilinear x2 upsampling of FP32
-32x64x128x128 fused with 3x3/s2/p1 max pooling of FP32 32x128x112x112 in one
-512-thread block per CTA.  One step = one fused launch over the whole batch.
-Before timing, a short sweep picks the split (1:3, 1:1, 3:1), the register
-cap and blocks/SM (Algorithm 2's knobs, Sec. 3.2).  Reported beside the
-fused time: the same two kernels launched back to back on one stream and on
-two concurrent streams (the native baseline of Sec. 4.1), and the ideal
-overlap bound max(total bytes / HBM bandwidth, ops / pipe peak).
+Default workload: eight uneven kernels in one persistent launch captured in a
+CUDA graph -- batch-norm statistics of FP32 64x256x56x56, im2col 3x3 of
+32x64x56x56, 3x3/s2/p1 max pooling of 32x128x112x112, bilinear x2 upsampling
+of 32x64x128x128, a 256-bin histogram of 2^26 bytes, 2^24 Philox4x32-10
+blocks, a 64-step degree-32 Horner chain on 2^22 floats and a bf16 scale+add
+of 2^27 elements.  One step = one graph launch of the autotuned fused plan
+over all eight.  Reported beside the fused time: the same kernels back to
+back on one stream and on eight concurrent streams (the native baseline of
+Sec. 4.1), the ideal-overlap bound max(total bytes / HBM bandwidth, ops /
+pipe peak), and three fused pairs measured the same way (fused vs serial vs
+two streams): batch-norm + polynomial (memory+compute, small), histogram +
+Philox (memory+compute) and upsample + max pool (memory+memory), each with
+the exhaustive search, Algorithm 2 (Sec. 3.2) and the naive even split.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload nway8|<pair>|cost_model|table2|ratio_sweep]
 """
 from __future__ import annotations
 
@@ -360,6 +366,52 @@ def pipelined_e2e(cx, slots, steps, warm=2):
     return e0.elapsed_time(e1) * 1e3 / steps
 
 
+def link_rates(cx, h2d, d2h, reps=3):
+    """Host-device link rates seen in this run: every input copied in alone
+    (one stream), every output copied out alone, then both directions at
+    once; best of `reps` each.  h2d = [(pinned host, device)], d2h =
+    [(device, pinned host)]."""
+    torch = cx.torch
+    s1, s2 = torch.cuda.Stream(device=cx.dev), torch.cuda.Stream(device=cx.dev)
+    nin = sum(d.numel() * d.element_size() for _, d in h2d)
+    nout = sum(d.numel() * d.element_size() for d, _ in d2h)
+
+    def once(do_in, do_out):
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(s1)
+        s2.wait_event(e0)
+        if do_in:
+            with torch.cuda.stream(s1):
+                for h, d in h2d:
+                    d.copy_(h, non_blocking=True)
+        if do_out:
+            with torch.cuda.stream(s2):
+                for d, h in d2h:
+                    h.copy_(d, non_blocking=True)
+        e1.record(s1)
+        e2.record(s2)
+        torch.cuda.synchronize()
+        return max(e0.elapsed_time(e1), e0.elapsed_time(e2)) * 1e3
+
+    t_in = min(once(True, False) for _ in range(reps))
+    t_out = min(once(False, True) for _ in range(reps))
+    t_both = min(once(True, True) for _ in range(reps))
+    return {"h2d_gbs": round(nin / (t_in * 1e3), 1), "d2h_gbs": round(nout / (t_out * 1e3), 1),
+            "h2d_alone_us": round(t_in, 1), "d2h_alone_us": round(t_out, 1),
+            "both_directions_us": round(t_both, 1)}
+
+
+def e2e_record(t_e2e, h2d, d2h, steps, link):
+    """The end-to-end object: per-step time with the copies inside the timed
+    region, the bytes each way, the link rates measured in the same run and
+    the copy-only bound they imply (both directions at once, per step)."""
+    return {"value": round(t_e2e, 2), "unit": "us", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": steps, "link": link,
+            "copy_bound_us": link["both_directions_us"],
+            "mode": "double-buffered: step i+1's inputs copy in while step i's outputs copy out"}
+
+
 def max_over_ranks(value, dist=None, device=None):
     """The slowest rank's time: every rank contributes its own and gets the
     maximum back (one all-reduce; replicas exchange nothing else)."""
@@ -371,7 +423,11 @@ def max_over_ranks(value, dist=None, device=None):
     return t.item()
 
 
-def run_pair(cx, name):
+def run_pair(cx, name, sub=False, peaks=None):
+    """One fused pair: exhaustive search, Algorithm 2, naive split, VFuse,
+    then the fused launch timed against serial and two-stream launches.
+    With sub=True it returns the compact record embedded in the default
+    line (no end-to-end leg)."""
     import torch
 
     from paper_2007_01277_gb300 import hfuse as H
@@ -452,6 +508,33 @@ def run_pair(cx, name):
                                          warm=Wm, flush=fl))
     H.hf_graph_destroy(g_fused)
 
+    hbm, peak_kind = measured_peaks()
+    peaks = peaks or pipe_peaks(H, st)
+    t_ideal, terms = ideal_us(nbytes, ops, peaks, hbm)
+    roofline = dominant_roofline(terms, nbytes, ops, peaks, t_fused, hbm, peak_kind,
+                                 load_traffic(spec["name"]))
+    info = H.hf_query(fused, args)
+    search = {"exhaustive_best_us": round(best["time_us"], 3), "points": len(ok),
+              "alg2": {k: alg2[k] for k in ("split", "regcap", "blocks_per_sm", "time_us")},
+              "naive_even_split_us": round(naive["time_us"], 3) if naive else None,
+              "vfuse_us": round(vfuse[0], 3) if vfuse else None,
+              "vfuse_block": vfuse[1] if vfuse else None}
+    cfg = {"split": best["split"], "d0": d0, "regcap": best["regcap"], "grid": grid,
+           "regs": info["regs"], "spill_bytes": info["spill_bytes"],
+           "l2": "L2 flushed (512 MB write) before every timed launch" if fl else
+                 "inputs larger than L2 (%.0f MB touched per step)" % _mb(nbytes)}
+    standalone = {H.BODY_NAMES[bodies[0]]: round(ta, 3), H.BODY_NAMES[bodies[1]]: round(tb, 3),
+                  "threads": [thr_a, thr_b]}
+    if sub:
+        rec = {"workload": spec["desc"], "fused_us": round(t_fused, 3), "serial_us": round(t_serial, 3),
+               "two_stream_us": round(t_two, 3), "fused_graph_us": round(t_graph, 3),
+               "fused_spread_us": spread(per), "standalone_us": standalone,
+               "speedup_vs_best_native": round(min(t_serial, t_two) / t_fused, 4),
+               "ideal_us": round(t_ideal, 3), "ideal_terms_us": terms,
+               "frac_of_ideal": round(t_ideal / t_fused, 4), "roofline": roofline,
+               "config": cfg, "search": search, "steps": K, "clocks": clk.summary()}
+        H.hf_destroy_fused(fused)
+        return rec
     # end to end: a second buffer set, inputs in and every output out per step
     _b2, args2, _n2, _o2, host_in2, outs2 = make_pair(name, H, W, cx.dev)
     slots = []
@@ -459,47 +542,37 @@ def run_pair(cx, name):
         hout = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs_]
         slots.append((hin, list(zip(outs_, hout)),
                       lambda s_, a_=a_: H.hf_launch(fused, a_, grid, s_)))
-    t_e2e = pipelined_e2e(cx, slots, max(6, K // 20))
+    t_e2e = pipelined_e2e(cx, slots, max(20, K))
     h2d = sum(d.numel() * d.element_size() for _, d in host_in)
     if "hashes" in spec:
         h2d += 80 * len(args)   # the headers travel in the launch's parameter block
     d2h = sum(o.numel() * o.element_size() for o in outs)
-
-    hbm, peak_kind = measured_peaks()
-    peaks = pipe_peaks(H, st)
-    t_ideal, terms = ideal_us(nbytes, ops, peaks, hbm)
-    roofline = dominant_roofline(terms, nbytes, ops, peaks, t_fused, hbm, peak_kind,
-                                 load_traffic(spec["name"]))
-    info = H.hf_query(fused, args)
+    link = link_rates(cx, slots[0][0], slots[0][1])
+    cfg["parallelism"] = "replicas" if cx.world > 1 else "single"
+    cfg["workload"] = spec["desc"]
     return {
         "metric": METRIC, "value": round(t_fused, 3), "unit": "us",
         "n_gpus": cx.world, "steps": K, "warmup": Wm, "ms_per_step": round(t_fused / 1e3, 6),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"hist_philox": "u8/u32"}.get(name, "u32/u64" if "hashes" in spec else "f32"), "data": "synthetic (seeded torch.Generator, CPU-drawn)",
-        "config": {"workload": spec["desc"], "split": best["split"], "d0": d0, "regcap": best["regcap"],
-                   "grid": grid, "regs": info["regs"], "spill_bytes": info["spill_bytes"],
-                   "l2": "L2 flushed (512 MB write) before every timed launch" if fl else
-                         "inputs larger than L2 (%.0f MB touched per step)" % _mb(nbytes),
-                   "parallelism": "replicas" if cx.world > 1 else "single"},
+        "dtype": {"hist_philox": "u8/u32"}.get(name, "u32/u64" if "hashes" in spec else "f32"),
+        "data": "synthetic (seeded torch.Generator, CPU-drawn)",
+        "config": cfg,
         "serial_us": round(t_serial, 3), "two_stream_us": round(t_two, 3),
         "fused_graph_us": round(t_graph, 3), "fused_spread_us": spread(per),
-        "standalone_us": {H.BODY_NAMES[bodies[0]]: round(ta, 3), H.BODY_NAMES[bodies[1]]: round(tb, 3),
-                          "threads": [thr_a, thr_b]},
+        "standalone_us": standalone,
         "speedup_vs_best_native": round(min(t_serial, t_two) / t_fused, 4),
         "ideal_us": round(t_ideal, 3), "ideal_terms_us": terms, "frac_of_ideal": round(t_ideal / t_fused, 4),
         "pipe_peaks_per_s": {k: float("%.4g" % v) for k, v in peaks.items()},
-        "search": {"exhaustive_best_us": round(best["time_us"], 3), "points": len(ok),
-                   "alg2": {k: alg2[k] for k in ("split", "regcap", "blocks_per_sm", "time_us")},
-                   "naive_even_split_us": round(naive["time_us"], 3) if naive else None,
-                   "vfuse_us": round(vfuse[0], 3) if vfuse else None,
-                   "vfuse_block": vfuse[1] if vfuse else None},
+        "search": search,
         "roofline": roofline,
-        "e2e": {"value": round(t_e2e, 2), "unit": "us", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "mode": "double-buffered: step i+1's inputs copy in while step i's outputs copy out"},
+        "e2e": e2e_record(t_e2e, h2d, d2h, max(20, K), link),
         "gpu_launches": K,
         "clocks": clk.summary(),
     }
 
+
+# the fused pairs reported inside the default (8-way) line
+SUB_PAIRS = ("bn_poly", "hist_philox", "upsample_maxpool")
 
 NWAY_DESC = ("8 kernels in one persistent CUDA-graph launch: bn stats 64x256x56x56, im2col 3x3 "
              "32x64x56x56, maxpool 32x128x112x112, upsample 32x64x128x128, hist 2^26 u8, "
@@ -610,16 +683,24 @@ def run_nway(cx):
         hout = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs_]
         slots.append((list(zip(hin, ins_)), list(zip(outs_, hout)),
                       lambda s_, g_=g_: H.hf_graph_launch(g_, s_)))
-    t_e2e = pipelined_e2e(cx, slots, max(6, K // 40))
-    e2e = {"value": round(t_e2e, 2), "unit": "us",
-           "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in ins),
-           "d2h_bytes_per_step": sum(t.numel() * t.element_size() for t in outs),
-           "mode": "double-buffered: step i+1's inputs copy in while step i's outputs copy out"}
+    t_e2e = pipelined_e2e(cx, slots, max(20, K))
+    e2e = e2e_record(t_e2e, sum(t.numel() * t.element_size() for t in ins),
+                     sum(t.numel() * t.element_size() for t in outs), max(20, K),
+                     link_rates(cx, slots[0][0], slots[0][1]))
     hbm, peak_kind = measured_peaks()
     peaks = pipe_peaks(H, st)
     t_ideal, terms = ideal_us(nbytes, ops, peaks, hbm)
     for g in graphs.values():
         H.hf_graph_destroy(g)
+    H.hf_graph_destroy(graph2)
+    H.hf_destroy_fused(fused)
+    # the fused pairs, each measured the same way (fused vs serial vs two
+    # streams, exhaustive search, Algorithm 2, naive split, VFuse)
+    pairs = {}
+    if not cx.args.no_pairs:
+        for nm in SUB_PAIRS:
+            pairs[nm] = run_pair(cx, nm, sub=True, peaks=peaks)
+            torch.cuda.empty_cache()
     return {
         "metric": METRIC, "value": round(t_fused, 3), "unit": "us",
         "n_gpus": cx.world, "steps": K, "warmup": Wm, "ms_per_step": round(t_fused / 1e3, 6),
@@ -636,6 +717,7 @@ def run_nway(cx):
         "roofline": dominant_roofline(terms, nbytes, ops, peaks, t_fused, hbm, peak_kind,
                                       load_traffic("nway8")),
         "e2e": e2e, "gpu_launches": K, "clocks": clk.summary(),
+        "pairs": pairs,
     }
 
 
@@ -723,44 +805,95 @@ def load_traffic(name):
 
 
 # ------------------------------------------------------------------ CPU oracle
-def cpu_baseline(seconds: float = 15.0, images: int | None = None):
-    """The oracle (plain C, double precision) on a bounded sample of the
-    same workload: `images` of the 32 images of both tensors, planes spread
-    over the host cores; the time is scaled to the full batch."""
-    from concurrent.futures import ThreadPoolExecutor
+def _ranges(n, parts):
+    """`parts` contiguous [lo, hi) ranges that cover 0 .. n-1 (empty ones dropped)."""
+    step = max(1, -(-n // max(1, parts)))
+    return [(lo, min(n, lo + step)) for lo in range(0, n, step)]
 
+
+_CPU_JOBS = {}
+
+
+def cpu_jobs(workload, cores):
+    """The oracle over the workload as independent jobs for `cores` host
+    threads: (jobs, scale, description).  Every kernel's input is cut into
+    about `cores` contiguous slices (images, channels, element or counter
+    ranges); the oracle's C routines release the interpreter lock, so the
+    slices run in parallel.  The deep-learning, histogram, Philox,
+    polynomial and bf16 workloads are computed whole (scale 1); the hash
+    scans on a fixed slice of their nonces, scaled.  Inputs are drawn once
+    and cached, outside any timing."""
+    key = (workload, cores)
+    if key in _CPU_JOBS:
+        return _CPU_JOBS[key]
     import numpy as np
 
     import oracle
     from paper_2007_01277_gb300 import workloads as W
+    jobs = []
 
-    cores = os.cpu_count() or 1
-    x_up = W.upsample_input(UP_SHAPE).numpy()
-    x_pool = W.maxpool_input(POOL_SHAPE).numpy()
-    # calibrate on one image, then size the sample to about `seconds`
-    def work(n_img):
-        jobs = []
-        for i in range(n_img):
-            for p in range(0, 64, 8):
-                jobs.append(("up", x_up[i, p:p + 8]))
-            for p in range(0, 128, 16):
-                jobs.append(("pool", x_pool[i, p:p + 16]))
+    def images(fn, x):
+        for lo, hi in _ranges(x.shape[0], cores):
+            jobs.append(lambda a=x[lo:hi]: fn(a))
 
-        def run(job):
-            kind, arr = job
-            return oracle.upsample2x(arr) if kind == "up" else oracle.maxpool3s2p1(arr)
+    def channels(x):
+        for lo, hi in _ranges(x.shape[1], cores):
+            jobs.append(lambda a=np.ascontiguousarray(x[:, lo:hi]): oracle.bn_stats(a))
 
-        t0 = time.perf_counter()
-        with ThreadPoolExecutor(cores) as ex:
-            list(ex.map(run, jobs))
-        return time.perf_counter() - t0
+    def flat(fn, x):
+        for lo, hi in _ranges(x.shape[0], cores):
+            jobs.append(lambda a=x[lo:hi]: fn(a))
 
-    t1 = work(1)
-    n = images or max(1, min(32, int(seconds / max(t1, 1e-3))))
-    t = work(n) if n > 1 else t1
-    us_full = t / n * 32 * 1e6
-    return {"value": round(us_full, 1), "unit": "us", "cores": cores, "kind": "oracle",
-            "sample": "%d of 32 images of both inputs (%.1f s), scaled x%.1f" % (n, t, 32 / n)}
+    def philox(n):
+        for lo, hi in _ranges(n, cores):
+            jobs.append(lambda lo=lo, hi=hi: oracle.philox4x32_10(0, hi - lo, first=lo))
+
+    coef = W.poly_coefficients().numpy()
+    poly = lambda a: oracle.poly(a, coef)
+    scale, desc = 1.0, "the whole workload"
+    if workload == "nway8":
+        sp = W.WORKLOADS["nway8"]
+        channels(W.bn_input(sp["bn"]).numpy())
+        images(oracle.im2col3, W.im2col_input(sp["im2col"]).numpy())
+        images(oracle.maxpool3s2p1, W.maxpool_input(sp["pool"]).numpy())
+        images(oracle.upsample2x, W.upsample_input(sp["up"]).numpy())
+        flat(oracle.hist256, W.hist_input(sp["hist_n"]).numpy())
+        philox(sp["philox_n"])
+        flat(poly, W.poly_input(sp["poly_n"]).numpy())
+        x16, y16 = (t.view(torch_int16()).numpy().view(np.uint16) for t in W.bf16_inputs(sp["bf16_n"]))
+        for lo, hi in _ranges(x16.shape[0], cores):
+            jobs.append(lambda a=x16[lo:hi], b=y16[lo:hi]: oracle.bf16_axpy(a, b, W.BF16_ALPHA))
+        desc = "the whole workload (all 8 kernels), each input cut into %d slices" % cores
+    elif workload == "upsample_maxpool":
+        images(oracle.upsample2x, W.upsample_input(UP_SHAPE).numpy())
+        images(oracle.maxpool3s2p1, W.maxpool_input(POOL_SHAPE).numpy())
+        desc = "the whole workload (both kernels), cut into image slices"
+    elif workload == "hist_philox":
+        flat(oracle.hist256, W.hist_input(1 << 28).numpy())
+        philox(1 << 26)
+        desc = "the whole workload (both kernels), cut into byte and counter ranges"
+    elif workload == "bn_poly":
+        channels(W.bn_input((8, 64, 32, 32)).numpy())
+        flat(poly, W.poly_input(1 << 20).numpy())
+        desc = "the whole workload (both kernels), cut into channel and element ranges"
+    elif workload in PAIR_SPECS and "hashes" in PAIR_SPECS[workload]:
+        scans = {"sha256d": oracle.sha256d_scan, "blake256": oracle.blake256_scan,
+                 "blake2b": oracle.blake2b_scan}
+        hs = PAIR_SPECS[workload]["hashes"]
+        per = 1 << 16
+        # the same fraction of each scan, so that one scale factor applies
+        frac = per / max(HASH_N[h] for h in hs)
+        for k, h in enumerate(hs):
+            n = max(cores, int(HASH_N[h] * frac))
+            hdr = W.hash_header(k)
+            for lo, hi in _ranges(n, cores):
+                jobs.append(lambda lo=lo, hi=hi, h=h, hdr=hdr: scans[h](hdr, lo, hi - lo))
+        scale = 1.0 / frac
+        desc = "%.4f of each scan's nonces, scaled x%.0f" % (frac, scale)
+    else:
+        return None
+    _CPU_JOBS[key] = (jobs, scale, desc)
+    return _CPU_JOBS[key]
 
 
 def _pool_time(jobs, cores):
@@ -771,73 +904,23 @@ def _pool_time(jobs, cores):
     return time.perf_counter() - t0
 
 
-def cpu_baseline_for(workload: str):
-    """The oracle on a bounded sample of `workload`, spread over the host
-    cores, scaled to the full workload.  Returns the cpu_baseline object."""
-    import numpy as np
+def cpu_sample_us(workload, cores):
+    """One timed run of the oracle on the workload's sample (us, scaled)."""
+    jobs, scale, _desc = cpu_jobs(workload, cores)
+    return _pool_time(jobs, cores) * scale * 1e6
 
-    import oracle
-    from paper_2007_01277_gb300 import workloads as W
+
+def cpu_baseline_for(workload: str, reps: int = 3):
+    """The cpu_baseline object: the median of `reps` runs of the oracle on
+    the workload's sample, spread over every host core.  The reference arm
+    times the same sample per step."""
     cores = os.cpu_count() or 1
-    if workload == "upsample_maxpool":
-        return cpu_baseline(seconds=10.0)
-    if workload == "hist_philox":
-        xs = W.hist_input(1 << 24).numpy()               # 1/16 of the bytes
-        chunks = np.array_split(xs, cores)
-        jobs = [lambda c=c: oracle.hist256(c) for c in chunks]
-        t_h = _pool_time(jobs, cores) * 16
-        per = (1 << 18) // cores                          # 1/256 of the blocks
-        jobs = [lambda i=i: oracle.philox4x32_10(0, per, first=i * per) for i in range(cores)]
-        t_p = _pool_time(jobs, cores) * (1 << 26) / (per * cores)
-        return {"value": round((t_h + t_p) * 1e6, 1), "unit": "us", "cores": cores, "kind": "oracle",
-                "sample": "hist on 2^24 of 2^28 bytes (x16), Philox on %d of 2^26 blocks" % (per * cores)}
-    if workload == "bn_poly":
-        x = W.bn_input((8, 64, 32, 32)).numpy()
-        t_b = _pool_time([lambda: oracle.bn_stats(x)], 1)
-        xq = W.poly_input(1 << 20).numpy()[: 1 << 14]
-        c = W.poly_coefficients().numpy()
-        chunks = np.array_split(xq, cores)
-        t_q = _pool_time([lambda ch=ch: oracle.poly(ch, c) for ch in chunks], cores) * 64
-        return {"value": round((t_b + t_q) * 1e6, 1), "unit": "us", "cores": cores, "kind": "oracle",
-                "sample": "bn on the whole input, poly on 2^14 of 2^20 elements (x64)"}
-    if workload in PAIR_SPECS and "hashes" in PAIR_SPECS[workload]:
-        scans = {"sha256d": oracle.sha256d_scan, "blake256": oracle.blake256_scan,
-                 "blake2b": oracle.blake2b_scan}
-        total, sample = 0.0, []
-        for k, h in enumerate(PAIR_SPECS[workload]["hashes"]):
-            per = (1 << 16) // cores
-            hdr = W.hash_header(k)
-            jobs = [lambda i=i, h=h, hdr=hdr: scans[h](hdr, i * per, per) for i in range(cores)]
-            total += _pool_time(jobs, cores) * HASH_N[h] / (per * cores)
-            sample.append("%s on %d of %d nonces" % (h, per * cores, HASH_N[h]))
-        return {"value": round(total * 1e6, 1), "unit": "us", "cores": cores, "kind": "oracle",
-                "sample": ", ".join(sample) + ", scaled"}
-    if workload == "nway8":
-        sp = W.WORKLOADS["nway8"]
-        parts = []
-        xb = W.bn_input((2,) + sp["bn"][1:]).numpy()                  # 2 of 64 images
-        parts.append((lambda: oracle.bn_stats(xb), 32))
-        xi = W.im2col_input((1,) + sp["im2col"][1:]).numpy()         # 1 of 32 images
-        parts.append((lambda: oracle.im2col3(xi), 32))
-        xp = W.maxpool_input((1,) + sp["pool"][1:]).numpy()
-        parts.append((lambda: oracle.maxpool3s2p1(xp), 32))
-        xu = W.upsample_input((1,) + sp["up"][1:]).numpy()
-        parts.append((lambda: oracle.upsample2x(xu), 32))
-        xh = W.hist_input(1 << 22).numpy()
-        parts.append((lambda: oracle.hist256(xh), 16))
-        parts.append((lambda: oracle.philox4x32_10(0, 1 << 16), 256))
-        xq = W.poly_input(1 << 12).numpy()
-        cq = W.poly_coefficients().numpy()
-        parts.append((lambda: oracle.poly(xq, cq), 1024))
-        x16, y16 = W.bf16_inputs(1 << 22)
-        b1, b2 = (t.view(torch_int16()).numpy().view(np.uint16) for t in (x16, y16))
-        parts.append((lambda: oracle.bf16_axpy(b1, b2, 0.5), 32))
-        total = 0.0
-        for fn, scale in parts:
-            total += _pool_time([fn], 1) * scale
-        return {"value": round(total * 1e6, 1), "unit": "us", "cores": 1, "kind": "oracle",
-                "sample": "each of the 8 kernels on a 1/16-1/1024 slice, single-threaded, scaled"}
-    return None
+    if cpu_jobs(workload, cores) is None:
+        return None
+    _jobs, _scale, desc = cpu_jobs(workload, cores)
+    v = statistics.median(cpu_sample_us(workload, cores) for _ in range(reps))
+    return {"value": round(v, 1), "unit": "us", "cores": cores, "kind": "oracle",
+            "sample": "%s; median of %d runs" % (desc, reps)}
 
 
 def torch_int16():
@@ -846,23 +929,31 @@ def torch_int16():
 
 
 def run_reference(args):
+    """The reference arm: the oracle (the paper has no code) timed on the
+    host cores, one run of the same sample as cpu_baseline per step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    steps = []
+    cores = os.cpu_count() or 1
+    got = cpu_jobs(args.workload, cores)
+    if got is None:
+        print(json.dumps({"impl": "reference", "unavailable": "no CPU oracle sample for workload "
+                          + args.workload}), flush=True)
+        return
+    desc = got[2]
     for _ in range(args.warmup):
-        cpu_baseline(images=1)
-    for _ in range(args.steps):
-        steps.append(cpu_baseline(images=1))
-    v = statistics.median(s["value"] for s in steps)
-    cb = dict(steps[0])
-    cb["value"] = v
+        cpu_sample_us(args.workload, cores)
+    per = [cpu_sample_us(args.workload, cores) for _ in range(args.steps)]
+    v = round(statistics.median(per), 1)
+    wl = NWAY_DESC if args.workload == "nway8" else PAIR_SPECS.get(args.workload, {}).get("desc", args.workload)
     line = {"metric": METRIC, "value": v, "unit": "us", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v / 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded torch.Generator, CPU-drawn)", "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": "1 of 32 images per step, scaled x32"},
-            "cpu_baseline": cb,
+            "config": {"workload": wl, "sample": desc},
+            "cpu_baseline": {"value": v, "unit": "us", "cores": cores, "kind": "oracle",
+                             "sample": "%s; median of %d steps" % (desc, args.steps)},
+            "step_spread_us": spread(per),
             "e2e": {"value": v, "unit": "us", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
@@ -876,11 +967,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="upsample_maxpool",
+    ap.add_argument("--workload", default="nway8",
                     choices=sorted(PAIR_SPECS) + ["nway8", "cost_model", "table2", "ratio_sweep"])
     ap.add_argument("--cost-db", default=None)
     ap.add_argument("--cost-steps", type=int, default=20000)
     ap.add_argument("--nway-evals", type=int, default=800)
+    ap.add_argument("--no-pairs", action="store_true",
+                    help="8-way workload only: skip the fused-pair records")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -229,6 +229,20 @@ void hf_destroy_kernel(hf_kernel k);
 hf_status hf_fuse(hf_kernel a, hf_kernel b, int split, int d0, int regcap,
                   hf_fused *out);
 
+/* hf_fuse without a register bound, from the checked build: the same two
+ * bodies in the same block layout, but every interval barrier (the
+ * "bar.sync id, d_k" that Sec. 3.1 puts in place of __syncthreads) is a
+ * software barrier over the interval's warps whose wait gives up after one
+ * second, setting bit 2 (value 2, a software barrier gave up) of the device
+ * error word (hf_check_device_error) instead of stalling the warps for good.  Use it to
+ * check a barrier schedule on the device without the risk of a hang; the
+ * results equal hf_fuse's.  Compiled for the pairs whose bodies have
+ * barriers: histogram + Philox, batch-norm + histogram, batch-norm +
+ * polynomial and stream template + stream template (either order);
+ * HF_ERR_UNSUPPORTED for any other pair.  Launch, query and destroy as any
+ * fused handle. */
+hf_status hf_fuse_checked(hf_kernel a, hf_kernel b, int split, int d0, hf_fused *out);
+
 /* N-way fusion into one persistent kernel.  n kernels ks[0..n) are placed on
  * n_intervals intervals of interval_threads[i] threads each (block size =
  * their sum); kernel j runs on interval interval_of[j], and kernels sharing
@@ -387,7 +401,11 @@ hf_status hf_autotune(hf_kernel a, hf_kernel b, const void *const *args, int d0,
  * HF_BN_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds
  * until the process exits.  The first call on a device looks up that
  * array's device address (once, with the device current); make that first
- * call before any stream capture.  Every call clears the counters at the
+ * call before any stream capture.  The address is kept for the life of the
+ * process, so the library must not be used across a reset of the device's
+ * context (cudaDeviceReset): later calls would use a stale address.  (The
+ * device error word of hf_check_device_error is looked up the same way.)
+ * Every call clears the counters at the
  * start of the array on `stream` and then launches; calls share the one
  * array, so calls whose work overlaps on the GPU (other streams, other host
  * threads) race and must be serialised by the caller.  Shapes whose scratch

@@ -28,6 +28,9 @@ struct Ctx {
     unsigned *err;       // the device's error word (bits below), or NULL
     unsigned ring_stage; // bulk-copy ring of this interval: stage bytes per warp
     int ring_stages;     //   and stages per warp (0: no ring, use register loads)
+#ifdef HF_CHECKED_BARRIERS
+    unsigned *chk_bar;   // checked build: the interval's two software-barrier words
+#endif
 };
 
 // Bits of the device error word read by hf_check_device_error().
@@ -52,6 +55,7 @@ __device__ __forceinline__ bool smem_fits(const Ctx &c, size_t bytes)
     return (size_t)(unsigned)__cvta_generic_to_shared(c.smem) + bytes <= (size_t)c.smem_end;
 }
 
+#ifndef HF_CHECKED_BARRIERS
 // The partial barrier of Sec. 3.1: only the d_k threads of this interval
 // arrive.  Intervals are whole warps, so every warp either executes it with
 // all its threads or not at all, as bar.sync requires.
@@ -59,6 +63,7 @@ __device__ __forceinline__ void interval_sync(const Ctx &c)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(c.bar), "r"(c.nthreads) : "memory");
 }
+#endif
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
@@ -102,6 +107,19 @@ __device__ __forceinline__ bool soft_barrier(unsigned *bar, int nwarps, unsigned
     __syncwarp();
     return ok;
 }
+
+#ifdef HF_CHECKED_BARRIERS
+// Checked build: the partial barrier of Sec. 3.1 becomes the bounded
+// software barrier above over the interval's warps, so a barrier schedule
+// whose count is never reached ends in kErrBarrierExpired after one second
+// instead of a hang.  The fused kernel's prologue zeroes the interval's two
+// words before any body runs.
+constexpr unsigned long long kCheckedBarrierLimitNs = 1000000000ull;
+__device__ __forceinline__ void interval_sync(const Ctx &c)
+{
+    soft_barrier(c.chk_bar, c.nthreads >> 5, c.err, kCheckedBarrierLimitNs);
+}
+#endif
 
 // Packed FP32 pairs: two floats in one 64-bit register and the f32x2
 // operations of sm_100 and later.  Each half is an ordinary correctly

@@ -15,6 +15,8 @@
 #pragma once
 #include <cstring>
 
+#include "hf_launch.h"
+
 #include "body_bn.cuh"
 #include "body_fp.cuh"
 #include "body_hash.cuh"
@@ -47,6 +49,12 @@ __device__ __forceinline__ void single_body(const SingleParams<B> &p)
     c.err = p.err;
     c.ring_stage = p.ring_stage;
     c.ring_stages = p.ring_stages;
+#ifdef HF_CHECKED_BARRIERS
+    __shared__ unsigned chk_bar[2];
+    if (threadIdx.x < 2) chk_bar[threadIdx.x] = 0u;
+    __syncthreads();
+    c.chk_bar = chk_bar;
+#endif
     B::run(p.a, c);
 }
 
@@ -99,6 +107,14 @@ __device__ __forceinline__ void pair_body(const PairParams<A, B> &p)
         c.ring_stage = p.ring_stage_high;
         c.ring_stages = p.ring_stages_high;
     }
+#ifdef HF_CHECKED_BARRIERS
+    // the two intervals' software-barrier words, zeroed by the whole block
+    // before it splits
+    __shared__ unsigned chk_bar[2][2];
+    if (threadIdx.x < 4) chk_bar[threadIdx.x >> 1][threadIdx.x & 1] = 0u;
+    __syncthreads();
+    c.chk_bar = chk_bar[low ? 0 : 1];
+#endif
     if (low == (p.low_is_a != 0))
         A::run(p.a, c);
     else
@@ -233,24 +249,8 @@ __global__ void __maxnreg__(R) k_nway_cap(const __grid_constant__ NwayParams p)
 // The device error word of the current device (runtime.cu), or NULL.
 unsigned *error_word();
 
-struct PairLaunch {
-    const void *const *args;   // [0] body A args, [1] body B args
-    int w_split, n_low, n_high;
-    unsigned smem_high, smem_total;
-    int low_is_a;
-    int grid, d0;
-    unsigned *err;
-    unsigned ring_stage[2];   // low, high interval
-    int ring_stages[2];
-};
-
-// Registry entry of one compiled instance.
-struct Instance {
-    int body_a, body_b;   // -1, -1 for the N-way kernel
-    int regcap;           // 0 = none
-    const void *func;     // the __global__ symbol
-    cudaError_t (*launch_pair)(const PairLaunch &, cudaStream_t);
-};
+using hfl::Instance;     // registry entry of one compiled instance
+using hfl::PairLaunch;   // arguments of one 2-way launch
 
 template <class A, class B, int R>
 const void *pair_func()

@@ -97,6 +97,7 @@ size_t align128(size_t v) { return (v + 127) / 128 * 128; }
 // ------------------------------------------------------------------ registry
 struct Registry {
     std::vector<Instance> pairs, nway;
+    std::vector<Instance> checked;   // pairs compiled with bounded software barriers
     std::vector<SingleEntry> singles;
     std::vector<int> caps;
 };
@@ -116,6 +117,8 @@ const Registry &registry()
         int n = 0;
         const Instance *p = nway_table(&n);
         r.nway.assign(p, p + n);
+        p = hfl::checked_pair_table(&n);
+        r.checked.assign(p, p + n);
         const SingleEntry *s = single_table(&n);
         r.singles.assign(s, s + n);
         for (auto &i : r.nway)
@@ -584,7 +587,13 @@ hf_status hf_register_kernel(const hf_kernel_desc *d, hf_kernel *out)
 
 void hf_destroy_kernel(hf_kernel k) { delete k; }
 
-hf_status hf_fuse(hf_kernel a, hf_kernel b, int split, int d0, int regcap, hf_fused *out)
+namespace {
+// Algorithm 1 for two registered kernels: validation, then the compiled
+// instance for (body pair, register cap) -- from the production instances,
+// or from the checked-barrier ones when `checked` is set (which have no
+// N-way fallback).
+hf_status fuse_pair(hf_kernel a, hf_kernel b, int split, int d0, int regcap, bool checked,
+                    hf_fused *out)
 {
     if (!a || !b || !out) return fail(HF_ERR_INVALID, "NULL kernel or output");
     if (d0 % 32 || split % 32 || split <= 0 || split >= d0 || d0 > 1024)
@@ -602,7 +611,7 @@ hf_status hf_fuse(hf_kernel a, hf_kernel b, int split, int d0, int regcap, hf_fu
     f->n_low = split;
     f->n_high = d0 - split;
     f->inst = nullptr;
-    for (auto &i : registry().pairs) {
+    for (auto &i : checked ? registry().checked : registry().pairs) {
         if (i.regcap != regcap) continue;
         if (i.body_a == a->body && i.body_b == b->body) {
             f->inst = &i;
@@ -614,6 +623,10 @@ hf_status hf_fuse(hf_kernel a, hf_kernel b, int split, int d0, int regcap, hf_fu
             f->low_is_a = 0;
             break;
         }
+    }
+    if (!f->inst && checked) {
+        delete f;
+        return fail(HF_ERR_UNSUPPORTED, "no checked-barrier instance of this body pair");
     }
     if (!f->inst) {   // no compiled pair: the generic N-way kernel with two intervals
         f->nway = true;
@@ -640,6 +653,17 @@ hf_status hf_fuse(hf_kernel a, hf_kernel b, int split, int d0, int regcap, hf_fu
     }
     *out = f;
     return HF_OK;
+}
+} // namespace
+
+hf_status hf_fuse(hf_kernel a, hf_kernel b, int split, int d0, int regcap, hf_fused *out)
+{
+    return fuse_pair(a, b, split, d0, regcap, false, out);
+}
+
+hf_status hf_fuse_checked(hf_kernel a, hf_kernel b, int split, int d0, hf_fused *out)
+{
+    return fuse_pair(a, b, split, d0, 0, true, out);
 }
 
 hf_status hf_fuse_n(const hf_kernel *ks, int n, const int *interval_of, const int *interval_threads,

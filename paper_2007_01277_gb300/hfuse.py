@@ -136,6 +136,7 @@ def _load():
         "hf_register_kernel": (_i32, [ctypes.POINTER(KernelDesc), ctypes.POINTER(_P)]),
         "hf_destroy_kernel": (None, [_P]),
         "hf_fuse": (_i32, [_P, _P, _i32, _i32, _i32, ctypes.POINTER(_P)]),
+        "hf_fuse_checked": (_i32, [_P, _P, _i32, _i32, ctypes.POINTER(_P)]),
         "hf_fuse_n": (_i32, [ctypes.POINTER(_P), _i32, ctypes.POINTER(_i32),
                              ctypes.POINTER(_i32), _i32, _i32, ctypes.POINTER(_P)]),
         "hf_destroy_fused": (None, [_P]),
@@ -236,6 +237,14 @@ def hf_register_kernel(body_id, min_threads=0, max_threads=0, granularity=0, nam
 def hf_fuse(a, b, split, d0, regcap=0):
     h = _P()
     _check("hf_fuse", lib.hf_fuse(a, b, split, d0, regcap, ctypes.byref(h)))
+    return h
+
+
+def hf_fuse_checked(a, b, split, d0):
+    """hf_fuse from the checked build: interval barriers are bounded
+    software barriers (an expired wait sets ERR_BARRIER_EXPIRED)."""
+    h = _P()
+    _check("hf_fuse_checked", lib.hf_fuse_checked(a, b, split, d0, ctypes.byref(h)))
     return h
 
 

@@ -84,6 +84,19 @@ def test_fuse_respects_kernel_ranges_and_caps(H):
     assert e.value.status == -6
 
 
+def test_fuse_checked_validation(H):
+    # the checked build validates like hf_fuse and exists only for pairs
+    # whose bodies have barriers; both are decided before any CUDA call
+    a, b = H.hf_register_kernel(H.HIST256), H.hf_register_kernel(H.PHILOX)
+    with pytest.raises(H.HFError) as e:
+        H.hf_fuse_checked(a, b, 100, 512)
+    assert e.value.status == -2
+    u, m = H.hf_register_kernel(H.UPSAMPLE2X), H.hf_register_kernel(H.MAXPOOL3S2)
+    with pytest.raises(H.HFError) as e:
+        H.hf_fuse_checked(u, m, 256, 512)
+    assert e.value.status == -6
+
+
 def test_fuse_n_validation(H):
     ks = [H.hf_register_kernel(H.POLY) for _ in range(3)]
     with pytest.raises(H.HFError) as e:       # 16 intervals: only 15 barrier ids

@@ -34,3 +34,20 @@ def test_spread():
     s = bench.spread([float(v) for v in range(1, 101)])
     assert s == {"median": 51.0, "p10": 11.0, "p90": 90.0}
     assert bench.spread([7.0]) == {"median": 7.0, "p10": 7.0, "p90": 7.0}
+
+
+def test_cpu_slices_cover_every_index_once():
+    for n in (0, 1, 7, 64, 100, 257):
+        for parts in (1, 3, 8, 16):
+            r = bench._ranges(n, parts)
+            assert [i for lo, hi in r for i in range(lo, hi)] == list(range(n))
+            assert len(r) <= parts and all(hi > lo for lo, hi in r)
+
+
+def test_reference_arm_and_cpu_baseline_time_the_same_sample():
+    # both go through cpu_jobs: same jobs, same description
+    jobs, scale, desc = bench.cpu_jobs("bn_poly", 4)
+    assert scale == 1.0 and "whole workload" in desc
+    # 64 channels and 2^20 elements in 4 slices each
+    assert len(jobs) == 8
+    assert bench.cpu_jobs("bn_poly", 4)[0] is jobs      # drawn once, cached

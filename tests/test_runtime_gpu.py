@@ -188,3 +188,63 @@ def test_soft_barrier_gives_up_on_a_missing_warp():
     for bad in ((0, -1, 1, 10), (33, -1, 1, 10), (4, 4, 1, 10), (4, -1, 0, 10), (4, -1, 1, 0)):
         with pytest.raises(H.HFError):
             H.hf_selftest_barrier(*bad)
+
+
+def _snapped_bound(ka, kb, args, d1, d0, lim, caps):
+    """The bound Algorithm 2 attaches to split d1 (Sec. 3.2): r0 from the
+    oracle's register-bound formula with the registers of each kernel
+    compiled alone and the fused kernel's shared memory, snapped down to
+    the nearest compiled cap (None when no cap lies at or below r0)."""
+    ra = H.hf_query_single(ka, args[0], d1)["regs"]
+    rb = H.hf_query_single(kb, args[1], d0 - d1)["regs"]
+    f0 = H.hf_fuse(ka, kb, d1, d0, 0)
+    smem = H.hf_query(f0, args)["smem_bytes"]
+    H.hf_destroy_fused(f0)
+    r0 = oracle.register_bound(lim.regs_per_sm, lim.smem_per_sm, lim.threads_per_sm, d1, ra,
+                               d0 - d1, rb, smem)
+    below = [c for c in caps if c <= r0]
+    return max(below) if below else None
+
+
+@pytest.mark.parametrize("d0,step", [(512, 128), (256, 64)])
+def test_alg2_pick_matches_oracle_search_on_its_own_trace(d0, step):
+    """hf_search_alg2's measured trace fed to oracle.alg2_search and to a
+    brute-force argmin: the visited (split, bound) sequence, r0 and the
+    pick (tie rule included) must agree exactly."""
+    x, px, coef, (m, v, y, _ws), args = _bn_poly()
+    ka, kb = H.hf_register_kernel(H.BN_STATS), H.hf_register_kernel(H.POLY)
+    lim = H.hf_device_info()
+    caps = H.hf_regcaps()
+    best, trace = H.hf_search_alg2(ka, kb, args, d0, step=step, reps=2)
+    bounds = {d1: _snapped_bound(ka, kb, args, d1, d0, lim, caps) for d1 in range(step, d0, step)}
+    # every split unbounded, then (if a compiled cap lies at or below r0) bounded
+    want = []
+    for d1 in range(step, d0, step):
+        want.append((d1, 0))
+        if bounds[d1] is not None:
+            want.append((d1, bounds[d1]))
+    assert [(p["split"], p["regcap"]) for p in trace] == want
+    inf = float("inf")
+    times = {(p["split"], p["regcap"]): (p["time_us"] if p["status"] == 0 else inf) for p in trace}
+    d_o, r_o, t_o = oracle.alg2_search(
+        d0, lambda d1, r: times.get((d1, 0 if r is None else r), inf), lambda d1: bounds[d1], step)
+    assert (best["split"], best["regcap"], best["time_us"]) == (d_o, 0 if r_o is None else r_o, t_o)
+    # brute force: the first point of the trace with the smallest time
+    first_min = min(range(len(trace)), key=lambda i: (times[(trace[i]["split"], trace[i]["regcap"])], i))
+    assert (trace[first_min]["split"], trace[first_min]["regcap"]) == (best["split"], best["regcap"])
+    # Algorithm 2's candidates at the blocks/SM it launches with are points of
+    # the exhaustive grid: the exhaustive table's argmin is never slower than
+    # the oracle's Algorithm 2 run over that same table
+    splits = list(range(step, d0, step))
+    cap_set = sorted({0} | {c for c in bounds.values() if c is not None})
+    table = H.hf_profile_pair(ka, kb, args, d0, splits, cap_set, [1, 2, 3, 4], reps=2)
+    ok = [p for p in table if p["status"] == 0]
+    occ = {}
+    for p in ok:
+        k = (p["split"], p["regcap"])
+        if k not in occ or p["blocks_per_sm"] > occ[k]["blocks_per_sm"]:
+            occ[k] = p
+    _d, _r, t_tab = oracle.alg2_search(
+        d0, lambda d1, r: occ[(d1, 0 if r is None else r)]["time_us"] if (d1, 0 if r is None else r) in occ
+        else inf, lambda d1: bounds[d1], step)
+    assert min(p["time_us"] for p in ok) <= t_tab
