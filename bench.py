@@ -701,6 +701,14 @@ def run_nway(cx):
         for nm in SUB_PAIRS:
             pairs[nm] = run_pair(cx, nm, sub=True, peaks=peaks)
             torch.cuda.empty_cache()
+    # the learned cost model on the same three pairs (trained on the
+    # built-in pairs at other sizes; regret read from the exhaustive table
+    # of the workload size), beside Algorithm 2 and the naive even split
+    cost = None
+    if not cx.args.no_pairs and not cx.args.no_cost_model:
+        from paper_2007_01277_gb300 import costmodel as CM
+        cost = CM.run_builtin(dev, hbm_gbs=hbm,
+                              log=lambda m: print(m, file=sys.stderr, flush=True))
     return {
         "metric": METRIC, "value": round(t_fused, 3), "unit": "us",
         "n_gpus": cx.world, "steps": K, "warmup": Wm, "ms_per_step": round(t_fused / 1e3, 6),
@@ -718,6 +726,7 @@ def run_nway(cx):
                                       load_traffic("nway8")),
         "e2e": e2e, "gpu_launches": K, "clocks": clk.summary(),
         "pairs": pairs,
+        "cost_model": cost,
     }
 
 
@@ -974,6 +983,8 @@ def main():
     ap.add_argument("--nway-evals", type=int, default=800)
     ap.add_argument("--no-pairs", action="store_true",
                     help="8-way workload only: skip the fused-pair records")
+    ap.add_argument("--no-cost-model", action="store_true",
+                    help="8-way workload only: skip the learned-model record")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

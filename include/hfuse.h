@@ -375,12 +375,27 @@ hf_status hf_search_alg2(hf_kernel a, hf_kernel b, const void *const *args, int 
  * to launch: mode HF_TUNE_EXHAUSTIVE profiles every split in warp steps
  * (32 .. d0 - 32, within both kernels' thread ranges) x every compiled
  * register cap and "none" x 1..4 blocks per SM and takes the fastest;
- * mode HF_TUNE_ALG2 runs hf_search_alg2 with step 128 (64 for d0 < 512).
+ * mode HF_TUNE_ALG2 runs hf_search_alg2 with step 128 (64 for d0 < 512);
+ * mode HF_TUNE_MODEL replaces Algorithm 2's profiling loop with the learned
+ * cost model installed by hf_cost_model_set: the same candidates as the
+ * exhaustive mode are built and queried (no launch), their features
+ * (hf_pair_features) scored in one hf_mlp_forward launch, and only the
+ * model's `confirm` best with distinct (split, blocks/SM) are timed, then
+ * the untimed neighbours of the fastest so far (its split with another
+ * blocks/SM or register cap, the splits one warp either side), again while
+ * that finds a faster one (at most three rounds); the fastest measured
+ * point is returned (HF_ERR_INVALID when no model is installed).
  * Timing as hf_time_fused (reps launches, L2 flushed when flush_l2).
  * HF_ERR_INVALID for an unknown mode or when no point can be launched. */
-enum { HF_TUNE_EXHAUSTIVE = 0, HF_TUNE_ALG2 = 1 };
+enum { HF_TUNE_EXHAUSTIVE = 0, HF_TUNE_ALG2 = 1, HF_TUNE_MODEL = 2 };
 hf_status hf_autotune(hf_kernel a, hf_kernel b, const void *const *args, int d0, int mode, int reps,
                       int flush_l2, void *stream, hf_tune_point *best);
+
+/* hf_autotune in HF_TUNE_MODEL mode that also reports how many candidates
+ * it timed (*n_timed, may be NULL): the model's `confirm` best plus the
+ * neighbour steps -- against every candidate for the exhaustive search. */
+hf_status hf_autotune_model(hf_kernel a, hf_kernel b, const void *const *args, int d0, int reps,
+                            int flush_l2, void *stream, hf_tune_point *best, int *n_timed);
 
 /* ------------------------------------------------------------------ */
 /* Allocation-free batch-norm statistics.                               */
@@ -559,6 +574,60 @@ hf_status hf_calibrate(int what, void *stream, double *ops_per_s);
 hf_status hf_tmpl_features(const hf_stream_tmpl_args *a, const hf_stream_tmpl_args *b, int split,
                            int d0, int regcap, int blocks_per_sm, int fused_regs, int spill_bytes,
                            double hbm_gbs, double ffma_per_s, float *out);
+
+/* Algorithmic work of one launch of a body on its arguments, the quantities
+ * of the ideal-overlap bound: the HBM bytes its definition moves (every
+ * input read once, every output written once) and its operations per
+ * pipe -- FP32 multiply-adds or FP32 operations, 32-bit integer
+ * multiplies, shared-memory atomics, 32-bit add/XOR/rotate operations --
+ * plus its barriers per tile.  Host arithmetic. */
+typedef struct {
+    double bytes;
+    double ffma;
+    double imul;
+    double smem_atomic;
+    double ialu;
+    int barriers;
+    int reserved;
+} hf_body_work;
+hf_status hf_body_work_of(int body_id, const void *args, hf_body_work *out);
+
+/* Measured pipe rates (hf_calibrate) and HBM bandwidth of the device. */
+typedef struct {
+    double hbm_gbs;
+    double ffma_per_s;
+    double imul_per_s;
+    double smem_atomic_per_s;
+    double ialu_per_s;
+} hf_pipe_peaks;
+
+/* The HF_MLP_FEATURES features of any two registered kernels fused in one
+ * d0-thread block (split threads for a, args[0] and args[1] their argument
+ * blocks), generalising hf_tmpl_features to every body: per kernel, its
+ * size (HBM bytes / 8), its operations per 32 bytes in FP32-FMA time
+ * (the busiest pipe's time over the FMA rate), barriers, the shared memory
+ * of its interval (with the bulk-copy ring the launch gives it at that
+ * occupancy), its roofline time alone max(bytes / HBM, busiest pipe),
+ * how compute-bound that is, its share of the block's threads, its warps
+ * per SM and its share of the pair's roofline time; then the configuration
+ * (register cap, blocks per SM, threads per SM, the fused instance's
+ * registers and spill bytes, shared memory per SM).  For two stream
+ * templates the result equals hf_tmpl_features.  Host arithmetic. */
+hf_status hf_pair_features(hf_kernel a, hf_kernel b, const void *const *args, int split, int d0,
+                           int regcap, int blocks_per_sm, int fused_regs, int spill_bytes,
+                           const hf_pipe_peaks *peaks, float *out);
+
+/* Installs the learned cost model used by hf_autotune(HF_TUNE_MODEL): an
+ * ensemble of n_models (1..16) perceptrons, params (host) holding their
+ * n_models * HF_MLP_NPARAMS floats back to back in the layout of
+ * hf_mlp_forward.  Each predicts (log(time) - log(t_ideal) - mu) / sd from
+ * hf_pair_features under `peaks`, t_ideal being the pair's ideal-overlap
+ * time (the same for every candidate of a pair, so only the ranking
+ * matters); candidates are ranked by the ensemble's mean prediction and the
+ * `confirm` (>= 1) best are timed.  The library keeps a copy; a later call
+ * replaces it, params = NULL removes it. */
+hf_status hf_cost_model_set(const float *params, int n_models, float mu, float sd,
+                            const hf_pipe_peaks *peaks, int confirm);
 
 /* FP32 perceptron 24 -> 64 -> ReLU -> 64 -> ReLU -> 1 over n rows of
  * X[n][24] (device), writing y[n] (device).  params (device) is the flat

@@ -31,6 +31,7 @@ import time
 import numpy as np
 import torch
 
+from . import experiments as _E
 from . import hfuse as H
 from . import workloads as W
 
@@ -214,3 +215,243 @@ def run(dev, db_path, n_pairs=600, n_train=500, steps=20000, reps=3, hbm_gbs=678
         "points_per_pair_exhaustive": len(SPLITS) * len(CAPS) * len(BPS),
     }
     return res, P, (mu, sd)
+
+
+# ------------------------------------------------------------------ built-in pairs
+# The model also learns from the library's own bodies: every pair type the
+# workloads fuse (batch-norm + polynomial, histogram + Philox, upsample +
+# max pool) and the ten Table-2 pairs of the deep-learning kernels, each
+# profiled exhaustively at sizes below its workload size.  The workload
+# sizes themselves are held out: the model's pick there is judged against
+# the exhaustive table of the same sizes.
+BUILTIN_PAIRS = {
+    "bn_poly": (("bn_small", "poly"), 512),
+    "hist_philox": (("hist_big", "philox"), 256),
+    "upsample_maxpool": (("upsample_big", "maxpool"), 512),
+}
+for _i, _a in enumerate(_E.DL_BODIES):
+    for _b in _E.DL_BODIES[_i + 1:]:
+        BUILTIN_PAIRS[_a + "_" + _b] = ((_a, _b), 512)
+BUILTIN_TARGETS = ("bn_poly", "hist_philox", "upsample_maxpool")
+# training sizes bracket the held-out workload size (scale 1)
+TRAIN_SCALES = (1 / 16, 1 / 8, 1 / 4, 1 / 2, 2, 4)
+BUILTIN_CAPS = (0, 32, 40, 48, 64, 96, 128)
+ENSEMBLE_SEEDS = (0, 1, 2)
+
+# Workload size of each kernel kind: (body, leading dimension or element
+# count, the rest of the shape).  Scaled kernels take a prefix of it.
+_KINDS = {
+    "bn_small": ("bn", 8, (64, 32, 32)), "poly": ("poly", 1 << 20, ()),
+    "hist_big": ("hist", 1 << 28, ()), "philox": ("philox", 1 << 26, ()),
+    "upsample_big": ("upsample", 32, (64, 128, 128)), "bn": ("bn", 64, (256, 56, 56)),
+    "hist": ("hist", 1 << 27, ()), "maxpool": ("maxpool", 32, (128, 112, 112)),
+    "upsample": ("upsample", 16, (64, 128, 128)), "im2col": ("im2col", 32, (64, 56, 56)),
+}
+
+
+class CorpusPool:
+    """Device buffers of every kernel kind at the largest scale, drawn on the
+    device (the corpus is only timed, never compared with the oracle, so the
+    values need the workloads' distributions but not their exact bytes);
+    scaled kernels use prefixes along the leading dimension."""
+
+    def __init__(self, dev, max_scale, seed=0):
+        self.dev, self.max_scale, self.buf = dev, max_scale, {}
+        self.g = torch.Generator(device=dev)
+        self.g.manual_seed(seed)
+
+    def _lead(self, kind, scale):
+        _body, n, _rest = _KINDS[kind]
+        return max(1, int(round(n * scale)))
+
+    def _get(self, kind):
+        if kind in self.buf:
+            return self.buf[kind]
+        body, _n, rest = _KINDS[kind]
+        L = self._lead(kind, self.max_scale)
+        dev, g = self.dev, self.g
+        if body == "bn":
+            b = {"x": torch.randn((L,) + rest, device=dev, generator=g)}
+        elif body == "poly":
+            b = {"x": torch.rand(L, device=dev, generator=g) * 2 - 1, "y": torch.empty(L, device=dev)}
+        elif body == "hist":
+            b = {"x": torch.randint(0, 256, (L,), device=dev, generator=g, dtype=torch.uint8)}
+        elif body == "philox":
+            b = {"y": torch.empty((L, 4), dtype=torch.int32, device=dev)}
+        elif body == "upsample":
+            b = {"x": torch.rand((L,) + rest, device=dev, generator=g),
+                 "y": torch.empty((L, rest[0], 2 * rest[1], 2 * rest[2]), device=dev)}
+        elif body == "maxpool":
+            b = {"x": torch.randn((L,) + rest, device=dev, generator=g),
+                 "y": torch.empty((L, rest[0], (rest[1] - 1) // 2 + 1, (rest[2] - 1) // 2 + 1), device=dev)}
+        else:   # im2col
+            b = {"x": torch.randn((L,) + rest, device=dev, generator=g),
+                 "y": torch.empty((L, rest[0] * 9, rest[1] * rest[2]), device=dev)}
+        self.buf[kind] = b
+        return b
+
+    def kernel(self, kind, scale):
+        """(body id, argument block) of `kind` at `scale` x its workload size."""
+        body, _n, rest = _KINDS[kind]
+        L = self._lead(kind, scale)
+        b = self._get(kind)
+        if body == "bn":
+            x = b["x"][:L]
+            m, v = torch.empty(rest[0], device=self.dev), torch.empty(rest[0], device=self.dev)
+            return H.BN_STATS, H.bn_stats_args(x, m, v, H.bn_stats_workspace(x))
+        if body == "poly":
+            return H.POLY, H.poly_args(b["x"][:L], b["y"][:L], W.poly_coefficients().tolist())
+        if body == "hist":
+            L16 = max(16, L // 16 * 16)
+            return H.HIST256, H.hist256_args(b["x"][:L16], torch.zeros(256, dtype=torch.int32, device=self.dev))
+        if body == "philox":
+            return H.PHILOX, H.philox_args(b["y"][:L], 0)
+        if body == "upsample":
+            return H.UPSAMPLE2X, H.upsample2x_args(b["x"][:L], b["y"][:L])
+        if body == "maxpool":
+            return H.MAXPOOL3S2, H.maxpool3s2_args(b["x"][:L], b["y"][:L])
+        return H.IM2COL3, H.im2col3_args(b["x"][:L], b["y"][:L])
+
+
+def builtin_grid(d0):
+    return list(range(32, d0, 32)), list(BUILTIN_CAPS), [1, 2, 3, 4]
+
+
+def profile_builtin(name, scale, pool, peaks, reps=3, stream=None, keep=False):
+    """Exhaustive profile of one built-in pair at one size: a record like
+    the template corpus's (points = [split, cap, bps, time, regs, spill,
+    status]) with the features (hf_pair_features) and log times of its valid
+    points.  The device tensors are released unless `keep` (then the
+    record holds the kernels and argument blocks for further launches)."""
+    (ka_kind, kb_kind), d0 = BUILTIN_PAIRS[name]
+    ba, aa = pool.kernel(ka_kind, scale)
+    bb, ab = pool.kernel(kb_kind, scale)
+    ka, kb = H.hf_register_kernel(ba), H.hf_register_kernel(bb)
+    splits, caps, bps = builtin_grid(d0)
+    table = H.hf_profile_pair(ka, kb, [aa, ab], d0, splits, caps, bps, reps=reps, flush_l2=False,
+                              stream=stream)
+    rec = {"name": name, "scale": scale, "d0": d0, "bodies": [ba, bb],
+           "points": [[q["split"], q["regcap"], q["blocks_per_sm"], round(q["time_us"], 3), q["regs"],
+                       q["spill_bytes"], q["status"]] for q in table]}
+    # target: log of the time over the pair's ideal-overlap time (constant
+    # per pair, so the ranking within a pair is that of the time itself)
+    rec["log_ideal"] = math.log(ideal_us([ba, bb], [aa, ab], peaks))
+    X, Y, qis = [], [], []
+    for qi, (split, cap, b_, t, regs, spill, st) in enumerate(rec["points"]):
+        if st != 0 or t <= 0:
+            continue
+        X.append(H.hf_pair_features(ka, kb, [aa, ab], split, d0, cap, b_, regs, spill, peaks))
+        Y.append(math.log(t) - rec["log_ideal"])
+        qis.append(qi)
+    rec["X"], rec["Y"], rec["qi"] = X, Y, qis
+    if keep:
+        rec["_kernels"], rec["_args"] = (ka, kb), [aa, ab]
+    else:
+        H.hf_destroy_kernel(ka)
+        H.hf_destroy_kernel(kb)
+    return rec
+
+
+def ideal_us(bodies, args, peaks):
+    """Ideal-overlap time of kernels run together (us): max(total bytes /
+    HBM bandwidth, each pipe's total operations / its rate)."""
+    tot = {"bytes": 0.0, "ffma": 0.0, "imul": 0.0, "smem_atomic": 0.0, "ialu": 0.0}
+    for b, a in zip(bodies, args):
+        w = H.hf_body_work_of(b, a)
+        for k in tot:
+            tot[k] += w[k]
+    rate = {"ffma": peaks.ffma_per_s, "imul": peaks.imul_per_s, "smem_atomic": peaks.smem_atomic_per_s,
+            "ialu": peaks.ialu_per_s}
+    t = tot["bytes"] / (peaks.hbm_gbs * 1e9)
+    for k, r in rate.items():
+        if r > 0:
+            t = max(t, tot[k] / r)
+    return t * 1e6
+
+
+def featurize_builtin(recs):
+    """Rows of (pair index, point index, features, log time) for the valid
+    points of built-in pair records."""
+    X, Y, owner = [], [], []
+    for pi, r in enumerate(recs):
+        X += r["X"]
+        Y += r["Y"]
+        owner += [(pi, qi) for qi in r["qi"]]
+    return np.asarray(X, np.float32), np.asarray(Y, np.float32), owner
+
+
+def device_peaks(hbm_gbs, stream=None):
+    """Measured HBM bandwidth plus the calibrated pipe rates of the device."""
+    return H.pipe_peaks(hbm_gbs, H.hf_calibrate(H.CAL_FFMA, stream), H.hf_calibrate(H.CAL_IMUL, stream),
+                        H.hf_calibrate(H.CAL_SMEM_ATOMIC, stream), H.hf_calibrate(H.CAL_IALU, stream))
+
+
+def run_builtin(dev, hbm_gbs=6785.9, steps=20000, reps=3, confirm=5, scales=TRAIN_SCALES,
+                seeds=ENSEMBLE_SEEDS, names=None, targets=BUILTIN_TARGETS, log=None):
+    """Trains an ensemble (one perceptron per seed) on the built-in pairs at
+    sizes bracketing their workload sizes, installs it for
+    hf_autotune(TUNE_MODEL), then judges it at the held-out workload sizes
+    of `targets`: the regret of the model's top-1 and top-`confirm` picks
+    read from the exhaustive table of that size, of the library's model mode
+    (which times its `confirm` best-scored candidates and the neighbours of
+    the fastest of them; its pick's time is read from the same table), of
+    Algorithm 2 and of the naive even split."""
+    names = list(names or BUILTIN_PAIRS)
+    st = torch.cuda.Stream(device=dev)
+    peaks = device_peaks(hbm_gbs, st)
+    pool = CorpusPool(dev, max(max(scales), 1.0))
+    t0 = time.time()
+    train_recs = []
+    for nm in names:
+        for sc in scales:
+            train_recs.append(profile_builtin(nm, sc, pool, peaks, reps=reps, stream=st))
+        if log:
+            log("profiled %s (%.0f s)" % (nm, time.time() - t0))
+    t_profile = time.time() - t0
+    Xtr, Ytr, _ = featurize_builtin(train_recs)
+    t1 = time.time()
+    models = [train(Xtr, Ytr, dev, steps=steps, seed=sd_) for sd_ in seeds]
+    t_train = time.time() - t1
+    mu, sd = models[0][1], models[0][2]   # the same standardisation for every seed
+    H.hf_cost_model_set([m[0] for m in models], mu, sd, peaks, confirm)
+    out = {"train_pairs": len(names), "train_sizes": [round(x, 4) for x in scales],
+           "train_points": int(Xtr.shape[0]), "ensemble": len(models), "confirm": confirm,
+           "profile_s": round(t_profile, 1), "train_s": round(t_train, 3),
+           "train_loss_first_last": [float(models[0][3][:100].mean()), float(models[0][3][-100:].mean())],
+           "pairs": {}}
+    for nm in targets:
+        rec = profile_builtin(nm, 1.0, pool, peaks, reps=reps, stream=st, keep=True)
+        X, Y, own = featurize_builtin([rec])
+        pred = np.mean([predict(m[0], X, mu, sd, dev) for m in models], axis=0)
+        ok = [q for q in rec["points"] if q[6] == 0 and q[3] > 0]
+        table = {(q[0], q[1], q[2]): q[3] for q in ok}
+        best = min(ok, key=lambda q: q[3])
+        ka, kb = rec["_kernels"]
+        d0 = rec["d0"]
+        tuned, n_timed = H.hf_autotune_model(ka, kb, rec["_args"], d0, reps=reps, stream=st)
+        key = (tuned["split"], tuned["regcap"], tuned["blocks_per_sm"])
+        a2, _trace = H.hf_search_alg2(ka, kb, rec["_args"], d0, step=128 if d0 >= 512 else 64, reps=reps,
+                                      flush_l2=False, stream=st)
+        a2_t = table.get((a2["split"], a2["regcap"], a2["blocks_per_sm"]))
+        naive = [q for q in ok if q[0] == d0 // 2 and q[1] == 0]
+        naive_t = min(naive, key=lambda q: -q[2])[3] if naive else None
+        rel = lambda t: round(t / best[3] - 1.0, 4) if t else None
+        out["pairs"][nm] = {
+            "points": len(ok), "rmse_log": round(float(np.sqrt(np.mean((pred - Y) ** 2))), 4),
+            "exhaustive_best": {"split": best[0], "regcap": best[1], "blocks_per_sm": best[2],
+                                "time_us": best[3]},
+            "model_regret_top1": round(float(regret([rec], own, pred, 1)[0]), 4),
+            "model_regret_top%d" % confirm: round(float(regret([rec], own, pred, confirm)[0]), 4),
+            "autotune_model": {"split": key[0], "regcap": key[1], "blocks_per_sm": key[2],
+                               "measured_us": round(tuned["time_us"], 3), "table_us": table.get(key),
+                               "regret": rel(table.get(key)), "timed_points": n_timed},
+            "alg2": {"split": a2["split"], "regcap": a2["regcap"], "blocks_per_sm": a2["blocks_per_sm"],
+                     "table_us": a2_t, "regret": rel(a2_t), "timed_points": len(_trace)},
+            "naive_even_split_regret": rel(naive_t),
+        }
+        H.hf_destroy_kernel(ka)
+        H.hf_destroy_kernel(kb)
+        del rec
+    del pool
+    torch.cuda.empty_cache()
+    return out

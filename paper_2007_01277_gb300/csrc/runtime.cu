@@ -232,6 +232,20 @@ struct hf_kernel_t {
     std::string name;
 };
 
+// Static facts of a body for the cost model's features (costmodel.cu).
+namespace hf {
+int kernel_body_id(const hf_kernel_t *k) { return k ? k->body : -1; }
+size_t body_smem_bytes(int id, int threads, const void *args)
+{
+    return valid_body(id) ? body_ops(id).smem(threads, args) : 0;
+}
+int body_barriers(int id) { return valid_body(id) ? body_ops(id).barriers : 0; }
+hf_status body_validate(int id, const void *args)
+{
+    return valid_body(id) ? body_ops(id).validate(args) : HF_ERR_INVALID;
+}
+} // namespace hf
+
 struct hf_fused_t {
     bool nway;
     int regcap;
@@ -391,6 +405,32 @@ hf_status plan_launch(const void *func, int d0, int n, const int *threads, const
     return fail(HF_ERR_REGS, "no resident configuration for a block of %d threads", d0);
 }
 
+} // namespace
+
+// Shared memory of each interval of a two-interval block at b blocks per SM
+// as the launch planner gives it: the body's slice plus the bulk-copy ring
+// the ring planner hands it at that occupancy (host arithmetic, no device
+// query; the cost model's features).
+namespace hf {
+void interval_smem_at(const int *ids, const void *const *args, const int *threads, int b, double *out)
+{
+    bool ring[2], use[2];
+    unsigned mins[2], stage = 0;
+    int warps[2], stages = 0;
+    for (int i = 0; i < 2; ++i) {
+        ring[i] = valid_body(ids[i]) && body_ops(ids[i]).ring(args[i]);
+        mins[i] = valid_body(ids[i]) ? body_ops(ids[i]).ring_min : 0u;
+        warps[i] = threads[i] / 32;
+    }
+    ring_choice(2, warps, ring, mins, b, use, &stage, &stages);
+    for (int i = 0; i < 2; ++i) {
+        const double base = valid_body(ids[i]) ? (double)body_ops(ids[i]).smem(threads[i], args[i]) : 0.0;
+        out[i] = base + (use[i] && stages > 0 ? (double)ring_bytes(threads[i], stage, stages) : 0.0);
+    }
+}
+} // namespace hf
+
+namespace {
 hf_status single_plan(const hf_kernel_t *k, const void *args, int threads, int want, LaunchPlan *plan)
 {
     const SingleEntry *e = find_single(k->body);

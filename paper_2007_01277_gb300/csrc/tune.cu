@@ -10,6 +10,7 @@
 // register-bound formula (snapped down to the nearest compiled cap), keeping
 // the first strictly faster configuration.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -500,10 +501,183 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
 
 } // extern "C"
 
+// ------------------------------------------------------------------ cost model
+// The learned replacement of Algorithm 2's profiling loop: every candidate
+// (split, register cap, blocks/SM) is built and queried on the host, scored
+// by the perceptron in one launch, and only the best-scored few are timed.
+namespace {
+struct CostModel {
+    std::vector<float> params;   // n_models parameter sets, back to back
+    int n_models = 0;
+    float mu = 0.f, sd = 1.f;
+    hf_pipe_peaks peaks{};
+    int confirm = 1;
+};
+std::mutex g_cm_mu;
+CostModel g_cm;
+bool g_cm_set = false;
+
+hf_status autotune_model_impl(hf_kernel a, hf_kernel b, const void *const *args, int d0, int reps,
+                              int flush_l2_, void *stream, hf_tune_point *best, int *n_timed)
+{
+    CostModel cm;
+    {
+        std::lock_guard<std::mutex> lk(g_cm_mu);
+        if (!g_cm_set) return HF_ERR_INVALID;
+        cm = g_cm;
+    }
+    if (d0 < 64 || d0 > 1024 || d0 % 32) return HF_ERR_INVALID;
+    hf_device_limits lim;
+    hf_status st = hf_device_info(&lim);
+    if (st) return st;
+    std::vector<int> caps = {0};
+    const int nc = hf_regcaps(nullptr, 0);
+    std::vector<int> compiled(nc > 0 ? nc : 0);
+    if (nc > 0) hf_regcaps(compiled.data(), nc);
+    caps.insert(caps.end(), compiled.begin(), compiled.end());
+    std::vector<hf_tune_point> cand;
+    std::vector<float> X;
+    for (int split = 32; split < d0; split += 32)
+        for (int cap : caps) {
+            hf_fused f = nullptr;
+            if (hf_fuse(a, b, split, d0, cap, &f)) continue;   // outside a kernel's range, ...
+            hf_fused_info info;
+            const hf_status qs = hf_query(f, args, &info);
+            hf_destroy_fused(f);
+            if (qs) continue;
+            for (int bps = 1; bps <= std::min(4, info.blocks_per_sm); ++bps) {
+                float feat[HF_MLP_FEATURES];
+                if (hf_pair_features(a, b, args, split, d0, cap, bps, info.regs, info.spill_bytes,
+                                     &cm.peaks, feat))
+                    continue;
+                hf_tune_point p;
+                std::memset(&p, 0, sizeof p);
+                p.split = split;
+                p.regcap = cap;
+                p.blocks_per_sm = bps;
+                p.grid = bps * lim.sm_count;
+                p.regs = info.regs;
+                p.spill_bytes = info.spill_bytes;
+                cand.push_back(p);
+                X.insert(X.end(), feat, feat + HF_MLP_FEATURES);
+            }
+        }
+    const int n = (int)cand.size();
+    if (n == 0) return HF_ERR_INVALID;
+    // one inference launch over every candidate
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float *dX = nullptr, *dy = nullptr, *dP = nullptr;
+    const int m = cm.n_models;
+    std::vector<float> ym((size_t)m * n), y(n, 0.f);
+    bool ok = cudaMalloc(&dX, X.size() * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&dy, (size_t)m * n * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&dP, cm.params.size() * sizeof(float)) == cudaSuccess &&
+              cudaMemcpyAsync(dX, X.data(), X.size() * sizeof(float), cudaMemcpyHostToDevice, s) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(dP, cm.params.data(), cm.params.size() * sizeof(float),
+                              cudaMemcpyHostToDevice, s) == cudaSuccess;
+    for (int k = 0; ok && k < m && st == HF_OK; ++k)
+        st = hf_mlp_forward(dP + (size_t)k * HF_MLP_NPARAMS, dX, n, dy + (size_t)k * n, stream);
+    ok = ok && st == HF_OK &&
+         cudaMemcpyAsync(ym.data(), dy, ym.size() * sizeof(float), cudaMemcpyDeviceToHost, s) ==
+             cudaSuccess &&
+         cudaStreamSynchronize(s) == cudaSuccess;
+    cudaFree(dX);
+    cudaFree(dy);
+    cudaFree(dP);
+    if (!ok) return st ? st : HF_ERR_CUDA;
+    for (int k = 0; k < m; ++k)   // the ensemble's mean prediction
+        for (int i = 0; i < n; ++i) y[i] += ym[(size_t)k * n + i] / (float)m;
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int i, int j) { return y[i] < y[j]; });
+    // time the model's best few, then the untimed neighbours of the fastest
+    // of them (other blocks/SM or register cap at its split, the splits one
+    // warp either side at its cap and blocks/SM); the fastest measured wins
+    best->time_us = -1.f;
+    std::vector<char> timed(n, 0);
+    int count = 0;
+    auto time_one = [&](int i) -> hf_status {
+        if (timed[i]) return HF_OK;
+        timed[i] = 1;
+        hf_tune_point p = cand[i];
+        hf_fused f = nullptr;
+        if (hf_fuse(a, b, p.split, d0, p.regcap, &f)) return HF_OK;
+        p.status = hf_time_fused(f, args, p.grid, reps, flush_l2_, stream, &p.time_us, &p.p10_us,
+                                 &p.p90_us);
+        hf_destroy_fused(f);
+        ++count;
+        if (p.status == HF_ERR_CUDA) return HF_ERR_CUDA;
+        if (!p.status && (best->time_us < 0.f || p.time_us < best->time_us)) *best = p;
+        return HF_OK;
+    };
+    // the `confirm` best-scored candidates with distinct (split, blocks/SM):
+    // candidates that differ only in the register cap score alike and are
+    // covered by the neighbour step
+    int confirmed = 0;
+    for (int r = 0; r < n && confirmed < cm.confirm; ++r) {
+        const hf_tune_point &q = cand[order[r]];
+        bool seen = false;
+        for (int i = 0; i < n && !seen; ++i)
+            seen = timed[i] && cand[i].split == q.split && cand[i].blocks_per_sm == q.blocks_per_sm;
+        if (seen) continue;
+        if (time_one(order[r]) == HF_ERR_CUDA) return HF_ERR_CUDA;
+        ++confirmed;
+    }
+    // neighbour steps from the fastest so far, while they find a faster one
+    for (int round = 0; round < 3 && best->time_us >= 0.f; ++round) {
+        const hf_tune_point c = *best;
+        for (int i = 0; i < n; ++i) {
+            const hf_tune_point &q = cand[i];
+            const bool same_split = q.split == c.split;
+            const bool nb = (same_split && q.regcap == c.regcap && q.blocks_per_sm != c.blocks_per_sm) ||
+                            (same_split && q.blocks_per_sm == c.blocks_per_sm && q.regcap != c.regcap) ||
+                            (std::abs(q.split - c.split) == 32 && q.regcap == c.regcap &&
+                             q.blocks_per_sm == c.blocks_per_sm);
+            if (nb && time_one(i) == HF_ERR_CUDA) return HF_ERR_CUDA;
+        }
+        if (best->split == c.split && best->regcap == c.regcap && best->blocks_per_sm == c.blocks_per_sm)
+            break;
+    }
+    if (n_timed) *n_timed = count;
+    return best->time_us < 0.f ? HF_ERR_INVALID : HF_OK;
+}
+} // namespace
+
+extern "C" hf_status hf_autotune_model(hf_kernel a, hf_kernel b, const void *const *args, int d0, int reps,
+                                       int flush_l2_, void *stream, hf_tune_point *best, int *n_timed)
+{
+    if (!a || !b || !args || !best || reps < 1) return HF_ERR_INVALID;
+    return autotune_model_impl(a, b, args, d0, reps, flush_l2_, stream, best, n_timed);
+}
+
+extern "C" hf_status hf_cost_model_set(const float *params, int n_models, float mu, float sd,
+                                       const hf_pipe_peaks *peaks, int confirm)
+{
+    std::lock_guard<std::mutex> lk(g_cm_mu);
+    if (!params) {
+        g_cm_set = false;
+        return HF_OK;
+    }
+    if (n_models < 1 || n_models > 16 || !peaks || confirm < 1 || !(sd > 0.f) || peaks->hbm_gbs <= 0 ||
+        peaks->ffma_per_s <= 0)
+        return HF_ERR_INVALID;
+    g_cm.params.assign(params, params + (size_t)n_models * HF_MLP_NPARAMS);
+    g_cm.n_models = n_models;
+    g_cm.mu = mu;
+    g_cm.sd = sd;
+    g_cm.peaks = *peaks;
+    g_cm.confirm = confirm;
+    g_cm_set = true;
+    return HF_OK;
+}
+
 extern "C" hf_status hf_autotune(hf_kernel a, hf_kernel b, const void *const *args, int d0, int mode,
                                  int reps, int flush_l2_, void *stream, hf_tune_point *best)
 {
     if (!a || !b || !args || !best || reps < 1) return HF_ERR_INVALID;
+    if (mode == HF_TUNE_MODEL)
+        return autotune_model_impl(a, b, args, d0, reps, flush_l2_, stream, best, nullptr);
     if (mode == HF_TUNE_ALG2)
         return hf_search_alg2(a, b, args, d0, d0 >= 512 ? 128 : 64, reps, flush_l2_, stream, best,
                               nullptr, 0, nullptr);

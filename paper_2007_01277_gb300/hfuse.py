@@ -120,6 +120,21 @@ class NwayPlan(ctypes.Structure):
                 "grid": self.grid, "time_us": self.time_us, "evals": self.evals}
 
 
+class BodyWork(ctypes.Structure):
+    _fields_ = [("bytes", ctypes.c_double), ("ffma", ctypes.c_double), ("imul", ctypes.c_double),
+                ("smem_atomic", ctypes.c_double), ("ialu", ctypes.c_double), ("barriers", _i32),
+                ("reserved", _i32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class PipePeaks(ctypes.Structure):
+    _fields_ = [("hbm_gbs", ctypes.c_double), ("ffma_per_s", ctypes.c_double),
+                ("imul_per_s", ctypes.c_double), ("smem_atomic_per_s", ctypes.c_double),
+                ("ialu_per_s", ctypes.c_double)]
+
+
 class HFError(RuntimeError):
     def __init__(self, fn, status, msg):
         super().__init__("%s -> %s: %s" % (fn, STATUS.get(status, status), msg))
@@ -189,6 +204,12 @@ def _load():
                                     _i32, _i32, _i32, _i32, _i32, _i32, ctypes.c_double,
                                     ctypes.c_double, ctypes.POINTER(_f32)]),
         "hf_mlp_forward": (_i32, [_P, _P, _i32, _P, _P]),
+        "hf_body_work_of": (_i32, [_i32, _P, ctypes.POINTER(BodyWork)]),
+        "hf_pair_features": (_i32, [_P, _P, _P, _i32, _i32, _i32, _i32, _i32, _i32,
+                                    ctypes.POINTER(PipePeaks), ctypes.POINTER(_f32)]),
+        "hf_autotune_model": (_i32, [_P, _P, _P, _i32, _i32, _i32, _P, ctypes.POINTER(TunePoint),
+                                     ctypes.POINTER(_i32)]),
+        "hf_cost_model_set": (_i32, [_P, _i32, _f32, _f32, ctypes.POINTER(PipePeaks), _i32]),
         "hf_mlp_train": (_i32, [_P, _P, _P, _P, _P, _P, _i32, _i32, _f32, _f32, _f32, _f32, _i32,
                                 _P, _P, _P]),
         "hf_mlp_nparams": (_i32, []),
@@ -628,7 +649,54 @@ def hf_selftest_barrier(warps, missing, rounds, limit_us, completed=None, stream
                                                           _stream_ptr(stream)))
 
 
-TUNE_EXHAUSTIVE, TUNE_ALG2 = 0, 1
+TUNE_EXHAUSTIVE, TUNE_ALG2, TUNE_MODEL = 0, 1, 2
+
+
+def hf_body_work_of(body_id, args):
+    """Algorithmic bytes and operations per pipe of one launch (dict)."""
+    w = BodyWork()
+    _check("hf_body_work_of", lib.hf_body_work_of(body_id, ctypes.cast(ctypes.pointer(args), _P),
+                                                  ctypes.byref(w)))
+    return w.as_dict()
+
+
+def pipe_peaks(hbm_gbs, ffma, imul, smem_atomic, ialu):
+    return PipePeaks(float(hbm_gbs), float(ffma), float(imul), float(smem_atomic), float(ialu))
+
+
+def hf_pair_features(a, b, args, split, d0, regcap, bps, fused_regs, spill_bytes, peaks):
+    out = (_f32 * MLP_FEATURES)()
+    _check("hf_pair_features", lib.hf_pair_features(a, b, _argv(args), split, d0, regcap, bps,
+                                                    fused_regs, spill_bytes, ctypes.byref(peaks), out))
+    return list(out)
+
+
+def hf_autotune_model(a, b, args, d0=512, reps=5, flush_l2=False, stream=None):
+    """hf_autotune(TUNE_MODEL) plus the number of candidates it timed:
+    returns (point dict, n_timed)."""
+    best = TunePoint()
+    n = _i32()
+    _check("hf_autotune_model", lib.hf_autotune_model(a, b, _argv(args), d0, reps, int(flush_l2),
+                                                      _stream_ptr(stream), ctypes.byref(best),
+                                                      ctypes.byref(n)))
+    return best.as_dict(), n.value
+
+
+def hf_cost_model_set(params, mu, sd, peaks, confirm=5):
+    """Installs the trained perceptron(s) for hf_autotune(..., TUNE_MODEL):
+    params is one float32 tensor of MLP_NPARAMS values or a list of them
+    (an ensemble whose mean prediction ranks the candidates); copied."""
+    if params is None:
+        _check("hf_cost_model_set", lib.hf_cost_model_set(None, 0, 0.0, 1.0, None, 1))
+        return
+    import numpy as np
+    sets = params if isinstance(params, (list, tuple)) else [params]
+    host = np.ascontiguousarray(np.concatenate([
+        np.asarray(p.detach().cpu() if hasattr(p, "detach") else p, dtype=np.float32).reshape(-1)
+        for p in sets]))
+    assert host.size == MLP_NPARAMS * len(sets)
+    _check("hf_cost_model_set", lib.hf_cost_model_set(host.ctypes.data_as(_P), len(sets), float(mu),
+                                                      float(sd), ctypes.byref(peaks), int(confirm)))
 
 
 def hf_autotune(a, b, args, d0=512, mode=TUNE_EXHAUSTIVE, reps=5, flush_l2=False, stream=None):

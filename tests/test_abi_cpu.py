@@ -168,3 +168,46 @@ def test_ring_plan_geometry(H):
     assert H.hf_ring_plan([4, 28], [0, 1], [1024, 1024], 1) == (1024, 2, [0, 1])
     with pytest.raises(H.HFError):
         H.hf_ring_plan([4], [1], [1024], 0)
+
+
+def test_pair_features_reduce_to_template_features(H):
+    """hf_pair_features generalises hf_tmpl_features: on two stream
+    templates the 24 features agree bit for bit (host arithmetic only)."""
+    import random
+    rng = random.Random(7)
+    kt1, kt2 = H.hf_register_kernel(H.STREAM_TMPL), H.hf_register_kernel(H.STREAM_TMPL)
+    pk = H.pipe_peaks(6785.9, 3.8e13, 1.75e13, 9.66e12, 3.0e13)
+    for _ in range(200):
+        def spec():
+            return H.StreamTmplArgs(None, None, 4 * rng.randint(1, 1 << 26), rng.choice([0, 1, 2, 4, 64, 256]),
+                                    rng.randint(0, 4), 16 * rng.randint(0, 3072), 0.999, 0.001)
+        a, b = spec(), spec()
+        d0 = rng.choice([256, 512, 1024])
+        split = 32 * rng.randint(1, d0 // 32 - 1)
+        cap, bps = rng.choice([0, 32, 64, 96]), rng.randint(1, 4)
+        regs, spill = rng.randint(24, 255), rng.choice([0, 16, 400])
+        want = H.hf_tmpl_features(a, b, split, d0, cap, bps, regs, spill, 6785.9, 3.8e13)
+        got = H.hf_pair_features(kt1, kt2, [a, b], split, d0, cap, bps, regs, spill, pk)
+        assert got == want
+
+
+def test_body_work_hand_values(H):
+    """Algorithmic bytes and operations of one launch, worked by hand."""
+    w = H.hf_body_work_of(H.BN_STATS, H.BnStatsArgs(None, None, None, 2, 3, 16, None))
+    assert (w["bytes"], w["ffma"]) == (4 * 96 + 8 * 3, 2 * 96)
+    w = H.hf_body_work_of(H.UPSAMPLE2X, H.Upsample2xArgs(None, None, 2, 4, 8))
+    assert w["bytes"] == 4 * 64 + 16 * 64
+    w = H.hf_body_work_of(H.MAXPOOL3S2, H.Maxpool3s2Args(None, None, 1, 5, 7))   # 5x7 -> 3x4
+    assert w["bytes"] == 4 * 35 + 4 * 12
+    w = H.hf_body_work_of(H.IM2COL3, H.Im2col3Args(None, None, 1, 2, 3, 4))
+    assert w["bytes"] == 4 * 24 * 10
+    w = H.hf_body_work_of(H.HIST256, H.Hist256Args(None, None, 1000))
+    assert (w["bytes"], w["smem_atomic"], w["barriers"]) == (2024, 1000, 2)
+    w = H.hf_body_work_of(H.PHILOX, H.PhiloxArgs(None, 10, 0, 0))
+    assert (w["bytes"], w["imul"]) == (160, 400)
+    w = H.hf_body_work_of(H.POLY, H.PolyArgs(None, None, 100, 64))
+    assert (w["bytes"], w["ffma"]) == (800, 100 * 64 * 33)
+    w = H.hf_body_work_of(H.BF16_AXPY, H.Bf16AxpyArgs(None, None, None, 50, 0.5))
+    assert w["bytes"] == 300
+    w = H.hf_body_work_of(H.STREAM_TMPL, H.StreamTmplArgs(None, None, 64, 8, 3, 0, 1.0, 0.0))
+    assert (w["bytes"], w["ffma"], w["barriers"]) == (512, 128, 3)

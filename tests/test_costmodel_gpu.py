@@ -93,3 +93,34 @@ def test_costmodel_pipeline_small():
     pred = CM.predict(P, X, mu, sd, DEV)
     r = CM.regret(recs, own, pred)
     assert r.shape == (6,) and np.all(r >= 0)
+
+
+def test_model_mode_needs_an_installed_model():
+    H.hf_cost_model_set(None, 0.0, 1.0, None)
+    x = torch.zeros(1 << 12, dtype=torch.uint8, device=DEV)
+    bins = torch.zeros(256, dtype=torch.int32, device=DEV)
+    po = torch.empty((256, 4), dtype=torch.int32, device=DEV)
+    kh, kx = H.hf_register_kernel(H.HIST256), H.hf_register_kernel(H.PHILOX)
+    with pytest.raises(H.HFError):
+        H.hf_autotune(kh, kx, [H.hist256_args(x, bins), H.philox_args(po, 0)], 256, H.TUNE_MODEL, reps=1)
+
+
+def test_model_mode_regret_on_the_workload_pairs():
+    """The learned replacement of Algorithm 2's profiling loop (Sec. 3.2) on
+    the library's own bodies: an ensemble trained on the built-in pairs at
+    sizes around (never at) the workload sizes drives hf_autotune_model --
+    one inference launch over every candidate, five distinct best-scored
+    candidates timed, then neighbour steps -- to a configuration of
+    batch-norm + polynomial, histogram + Philox and upsample + max pool whose
+    time in the exhaustive table of the workload size is within 5 % of that
+    table's best, timing under a fifth of the candidates the exhaustive
+    search times."""
+    res = CM.run_builtin(DEV)
+    assert res["train_points"] > 5000 and res["ensemble"] == 3
+    for nm in CM.BUILTIN_TARGETS:
+        r = res["pairs"][nm]
+        tuned = r["autotune_model"]
+        assert tuned["table_us"] is not None, (nm, r)
+        assert tuned["regret"] <= 0.05, (nm, r)
+        assert tuned["timed_points"] < 0.2 * r["points"], (nm, r)
+    H.hf_cost_model_set(None, 0.0, 1.0, None)
