@@ -443,8 +443,8 @@ def run_pair(cx, name, sub=False, peaks=None):
                               list(spec["bps"]), reps=5, flush_l2=fl, stream=st)
     ok = [p for p in table if p["status"] == 0]
     best = min(ok, key=lambda p: p["time_us"])
-    alg2, _trace = H.hf_search_alg2(ka, kb, args, d0, step=128 if d0 >= 512 else 64, reps=5,
-                                    flush_l2=fl, stream=st)
+    alg2, a2_trace = H.hf_search_alg2(ka, kb, args, d0, step=128 if d0 >= 512 else 64, reps=5,
+                                      flush_l2=fl, stream=st)
     naive = [p for p in ok if p["split"] == d0 // 2 and p["regcap"] == 0]
     naive = min(naive, key=lambda p: -p["blocks_per_sm"]) if naive else None
     # vertical fusion (Sec. 2.2): every thread runs one kernel, then the other
@@ -516,6 +516,10 @@ def run_pair(cx, name, sub=False, peaks=None):
     info = H.hf_query(fused, args)
     search = {"exhaustive_best_us": round(best["time_us"], 3), "points": len(ok),
               "alg2": {k: alg2[k] for k in ("split", "regcap", "blocks_per_sm", "time_us")},
+              "alg2_trace": [[p[k] for k in ("split", "regcap", "blocks_per_sm", "regs", "spill_bytes")]
+                             + [round(p["time_us"], 2)] for p in a2_trace],
+              "exhaustive_best": {k: best[k] for k in ("split", "regcap", "blocks_per_sm", "regs",
+                                                       "spill_bytes")},
               "naive_even_split_us": round(naive["time_us"], 3) if naive else None,
               "vfuse_us": round(vfuse[0], 3) if vfuse else None,
               "vfuse_block": vfuse[1] if vfuse else None}

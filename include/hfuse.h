@@ -380,7 +380,8 @@ hf_status hf_search_alg2(hf_kernel a, hf_kernel b, const void *const *args, int 
  * cost model installed by hf_cost_model_set: the same candidates as the
  * exhaustive mode are built and queried (no launch), their features
  * (hf_pair_features) scored in one hf_mlp_forward launch, and only the
- * model's `confirm` best with distinct (split, blocks/SM) are timed, then
+ * model's best at each blocks/SM and its `confirm` best with distinct
+ * (split, blocks/SM) are timed, then
  * the untimed neighbours of the fastest so far (its split with another
  * blocks/SM or register cap, the splits one warp either side), again while
  * that finds a faster one (at most three rounds); the fastest measured

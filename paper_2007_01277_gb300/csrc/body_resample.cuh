@@ -180,6 +180,16 @@ struct BodyMaxpool {
     static constexpr int kId = HF_BODY_MAXPOOL3S2;
     static constexpr int kRows = 8;    // output rows per warp strip
     static constexpr int kBarriers = 0;
+    // ring path: a stage must hold the 9 input rows of a strip of 4 output
+    // rows (rows of up to 128 floats)
+    static constexpr unsigned kRingMinBytes = 4096;
+
+    // strips of whole rows (W <= 128, 16-byte rows) arrive as one bulk copy
+    static __host__ bool uses_ring(const Args &a)
+    {
+        return (int64_t)a.P * a.H * a.W > 0 && (a.W & 3) == 0 && a.W <= 128 && a.H >= 2 &&
+               aligned16(a.x) && aligned16(a.y);
+    }
 
     static __host__ size_t workspace_bytes(const Args &) { return 0; }
     static __host__ size_t smem_bytes(int, const Args &) { return 0; }
@@ -253,6 +263,96 @@ struct BodyMaxpool {
         }
     }
 
+    // Ring path.  Work item = (plane, strip of R = 4 output rows); its
+    // input rows [max(2*o0-1, 0), min(2*o1, H)) are contiguous and arrive
+    // in one bulk copy in a stage of the warp's ring, the next items' copies
+    // in flight meanwhile.  Lane l takes input columns 4l..4l+3 (output
+    // columns 2l, 2l+1) of each of the strip's nine rows from shared memory
+    // (nine independent loads); the left halo column comes from lane l-1 by
+    // shuffle.  No loads are held in registers, so bytes in flight do not
+    // depend on registers or warps.
+    static constexpr int kRingRows = 4;   // output rows per ring work item
+
+    // (plane, strip) of a warp's items, advanced by the constant item stride
+    // without divisions.
+    struct Cursor {
+        unsigned p, s;
+        __device__ void init(int64_t it, unsigned ns)
+        {
+            p = (unsigned)(it / ns);
+            s = (unsigned)(it - (int64_t)p * ns);
+        }
+        __device__ void step(unsigned dq, unsigned dr, unsigned ns)
+        {
+            s += dr;
+            p += dq;
+            if (s >= ns) s -= ns, ++p;
+        }
+    };
+
+    static __device__ bool run_ring(const Args &a, const Ctx &cx)
+    {
+        constexpr int R = kRingRows, NR = 2 * R + 1;
+        const int H = a.H, W = a.W, Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1;
+        const unsigned row_bytes = 4u * (unsigned)W;
+        if (cx.ring_stage < NR * row_bytes || (int64_t)a.P * H >= ((int64_t)1 << 32)) return false;
+        const unsigned ns = (unsigned)((Ho + R - 1) / R);
+        const int64_t items = (int64_t)a.P * ns;
+        WarpRing r;
+        r.init(cx, 0);
+        const int nw = cx.nthreads >> 5;
+        const int64_t gw = (int64_t)cx.block * nw + (cx.tid >> 5), GW = (int64_t)cx.grid * nw;
+        const unsigned dq = (unsigned)(GW / ns), dr = (unsigned)(GW % ns);
+        const int lane = lane_id();
+        const int c0 = 4 * lane;
+        const bool act = c0 < W;
+        const float ninf = -__int_as_float(0x7f800000);
+        Cursor fc, uc;   // the fill cursor runs S items ahead of the use cursor
+        fc.init(gw, ns);
+        uc = fc;
+        ring_stream(
+            r, gw, GW, items,
+            [&](int st, int64_t) {
+                const int o0 = (int)fc.s * R, o1 = min(o0 + R, Ho);
+                const int ylo = max(2 * o0 - 1, 0), yhi = min(2 * o1, H);
+                const unsigned first_row = fc.p * (unsigned)H + (unsigned)ylo;
+                const unsigned bytes = (unsigned)(yhi - ylo) * row_bytes;   // rows are 16-byte multiples
+                r.expect(st, bytes);
+                r.copy(st, 0, a.x + (uint64_t)first_row * W, bytes);
+                fc.step(dq, dr, ns);
+            },
+            [&](const unsigned char *stage, int64_t) {
+                const int o0 = (int)uc.s * R, o1 = min(o0 + R, Ho);
+                const int ylo = max(2 * o0 - 1, 0), yhi = min(2 * o1, H);
+                // rows 2*o0-1 .. 2*o0+2R-1 at clamped (in-stage) offsets,
+                // lanes past W reading column 0; row 2*o0-1 is padding in
+                // the first strip and rows at or past H (odd H) in the last
+                const unsigned char *base = stage + (act ? 4 * c0 : 0);
+                float2 h[NR];
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    const int y = min(max(2 * o0 - 1 + k, ylo), yhi - 1);
+                    const float4 q = *reinterpret_cast<const float4 *>(base + (unsigned)(y - ylo) * row_bytes);
+                    float L = __shfl_up_sync(0xffffffffu, q.w, 1);
+                    if (lane == 0) L = ninf;
+                    h[k] = make_float2(mx(mx(L, q.x), q.y), mx(mx(q.y, q.z), q.w));
+                }
+                if (o0 == 0) h[0] = make_float2(ninf, ninf);
+#pragma unroll
+                for (int k = 1; k < NR; ++k)
+                    if (2 * o0 - 1 + k >= yhi) h[k] = make_float2(ninf, ninf);
+                float *yp = a.y + ((int64_t)uc.p * Ho + o0) * Wo + (c0 >> 1);
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    if (act && o0 + j < o1)
+                        stcs2(yp + j * Wo, make_float2(mx(mx(h[2 * j].x, h[2 * j + 1].x), h[2 * j + 2].x),
+                                                       mx(mx(h[2 * j].y, h[2 * j + 1].y), h[2 * j + 2].y)));
+                uc.step(dq, dr, ns);
+            });
+        r.finish();
+        return true;
+    }
+
     static __device__ void run_scalar(const Args &a, const Ctx &cx)
     {
         const int H = a.H, W = a.W, Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1;
@@ -281,10 +381,12 @@ struct BodyMaxpool {
     static __device__ void run(const Args &a, const Ctx &cx)
     {
         if ((int64_t)a.P * a.H * a.W == 0) return;
-        if ((a.W & 3) == 0 && aligned16(a.x) && aligned16(a.y))
+        if ((a.W & 3) == 0 && aligned16(a.x) && aligned16(a.y)) {
+            if (a.W <= 128 && a.H >= 2 && WarpRing::available(cx, 0) && run_ring(a, cx)) return;
             run_vec(a, cx);
-        else
+        } else {
             run_scalar(a, cx);
+        }
     }
 };
 

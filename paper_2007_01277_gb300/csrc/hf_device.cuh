@@ -294,25 +294,27 @@ struct WarpRing {
     // before the copy engine's writes.
     __device__ void refill_fence() const { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-    // All lanes: wait for stage s's phase `parity`.  The decision is taken
+    // All lanes: wait for stage s's phase `parity`.  Each try suspends the
+    // thread in hardware until the phase completes or kSuspendNs pass (a
+    // try without the hint returns at once, and a warp spinning on it takes
+    // issue slots from the warps that compute); the expiry decision is taken
     // for the whole warp (vote and lane 0's clock), so lanes never diverge.
+    static constexpr unsigned kSuspendNs = 200000;
     __device__ bool wait(int s, unsigned parity) const
     {
         unsigned long long t0 = 0;
         for (unsigned it = 0;; ++it) {
             unsigned done;
             asm volatile("{\n\t.reg .pred p;\n\t"
-                         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
                          "selp.u32 %0, 1, 0, p;\n\t}"
                          : "=r"(done)
-                         : "r"(bars + 8u * s), "r"(parity)
+                         : "r"(bars + 8u * s), "r"(parity), "n"(kSuspendNs)
                          : "memory");
             if (__all_sync(0xffffffffu, done)) return true;
-            if ((it & 63u) == 63u) {
-                const unsigned long long now = __shfl_sync(0xffffffffu, timer_ns(), 0);
-                if (t0 == 0) t0 = now;
-                else if (now - t0 > limit_ns) return false;
-            }
+            const unsigned long long now = __shfl_sync(0xffffffffu, timer_ns(), 0);
+            if (it == 0) t0 = now;
+            else if (now - t0 > limit_ns) return false;
         }
     }
     // All lanes, after the last wait: release the barriers' memory.

@@ -611,9 +611,16 @@ hf_status autotune_model_impl(hf_kernel a, hf_kernel b, const void *const *args,
         if (!p.status && (best->time_us < 0.f || p.time_us < best->time_us)) *best = p;
         return HF_OK;
     };
-    // the `confirm` best-scored candidates with distinct (split, blocks/SM):
-    // candidates that differ only in the register cap score alike and are
-    // covered by the neighbour step
+    // the best-scored candidate at each blocks/SM (the coordinate the model
+    // ranks least reliably), then the `confirm` best-scored candidates with
+    // distinct (split, blocks/SM): candidates that differ only in the
+    // register cap score alike and are covered by the neighbour step
+    for (int b = 1; b <= 4; ++b)
+        for (int r = 0; r < n; ++r)
+            if (cand[order[r]].blocks_per_sm == b) {
+                if (time_one(order[r]) == HF_ERR_CUDA) return HF_ERR_CUDA;
+                break;
+            }
     int confirmed = 0;
     for (int r = 0; r < n && confirmed < cm.confirm; ++r) {
         const hf_tune_point &q = cand[order[r]];

@@ -109,8 +109,9 @@ def test_model_mode_regret_on_the_workload_pairs():
     """The learned replacement of Algorithm 2's profiling loop (Sec. 3.2) on
     the library's own bodies: an ensemble trained on the built-in pairs at
     sizes around (never at) the workload sizes drives hf_autotune_model --
-    one inference launch over every candidate, five distinct best-scored
-    candidates timed, then neighbour steps -- to a configuration of
+    one inference launch over every candidate, the best-scored candidate at
+    each blocks/SM and five distinct best-scored ones timed, then neighbour
+    steps -- to a configuration of
     batch-norm + polynomial, histogram + Philox and upsample + max pool whose
     time in the exhaustive table of the workload size is within 5 % of that
     table's best, timing under a fifth of the candidates the exhaustive
