@@ -514,12 +514,16 @@ hf_status hf_src_query(hf_src_module m, int *regs, int *local_bytes, int *static
 void hf_src_unload(hf_src_module m);
 
 /* The bulk-copy ring geometry the launch planner gives a block of n
- * intervals (warps[i] warps; ring[i] != 0 when its kernel can stream
- * through a ring and wants at least min_bytes[i] in flight per warp) at
- * blocks_per_sm resident blocks: about 40 KB in flight per SM over the ring
- * warps, intervals whose minimum the share misses fall back to register
- * loads (uses[i] = 0), stages of 1, 2 or 4 KB, 2 to 4 per warp; stages = 0
- * when no interval keeps a ring.  Host arithmetic only. */
+ * intervals (warps[i] warps) at blocks_per_sm resident blocks.  ring[i] is
+ * the kind of ring interval i's kernel takes: 0 none; 1 a stream ring --
+ * whole tiles of a flat array, wanting at least min_bytes[i] in flight per
+ * warp; 2 an item ring -- one work item (min_bytes[i] bytes) per stage.
+ * Item rings get two stages of min_bytes[i] (rounded up to 128) per warp.
+ * Stream rings share about 40 KB in flight per SM over their warps, in
+ * stages of 1, 2 or 4 KB, 2 to 4 per warp; intervals whose minimum the
+ * share misses fall back to register loads.  Per interval: stage[i] bytes,
+ * stages[i] (0 when no ring) and uses[i].  The launch drops item rings
+ * first if they do not fit in shared memory.  Host arithmetic only. */
 hf_status hf_ring_plan(int n, const int *warps, const int *ring, const unsigned *min_bytes,
                        int blocks_per_sm, unsigned *stage, int *stages, int *uses);
 

@@ -14,6 +14,23 @@
 
 namespace hf {
 
+// (plane, strip) of a warp's ring work items -- items it, it + step, ...
+// with it = plane * ns + strip -- advanced without divisions.
+struct ItemCursor {
+    unsigned p, s;
+    __device__ void init(int64_t it, unsigned ns)
+    {
+        p = (unsigned)(it / ns);
+        s = (unsigned)(it - (int64_t)p * ns);
+    }
+    __device__ void step(unsigned dq, unsigned dr, unsigned ns)   // step = dq * ns + dr
+    {
+        s += dr;
+        p += dq;
+        if (s >= ns) s -= ns, ++p;
+    }
+};
+
 // ------------------------------------------------------------------------
 // Bilinear x2, half-pixel centres.  Along one axis of length L, output 2i
 // blends input i-1 and i with weights 1/4, 3/4 (output 0 is input 0) and
@@ -26,6 +43,18 @@ struct BodyUpsample {
     static constexpr int kId = HF_BODY_UPSAMPLE2X;
     static constexpr int kRows = 8;    // input rows per warp strip
     static constexpr int kBarriers = 0;
+    // ring path: a stage holds the 6 input rows of an item and its two halo
+    // rows (rows of up to 128 floats)
+    static constexpr int kRingRows = 6;
+    static constexpr bool kRingItem = true;
+    static constexpr unsigned kRingMinBytes = 4096;   // the stage: one item
+
+    // strips of whole rows (W <= 128, 16-byte rows) arrive as one bulk copy
+    static __host__ bool uses_ring(const Args &a)
+    {
+        return (int64_t)a.P * a.H * a.W > 0 && (a.W & 3) == 0 && a.W <= 128 && aligned16(a.x) &&
+               aligned16(a.y);
+    }
 
     static __host__ size_t workspace_bytes(const Args &) { return 0; }
     static __host__ size_t smem_bytes(int, const Args &) { return 0; }
@@ -135,6 +164,89 @@ struct BodyUpsample {
         }
     }
 
+    // Ring path.  Work item = (plane, strip of R = 6 input rows); the strip
+    // and its halo rows, [max(r0-1, 0), min(r0+R+1, H)), are contiguous and
+    // arrive in one bulk copy in a stage of the warp's ring while the next
+    // items' copies are in flight.  Lane l takes input columns 4l..4l+3 of
+    // each row from shared memory (the halo columns from lanes l-1 and l+1
+    // by shuffle; a band is the whole row, so lane 0's left and the last
+    // lane's right column are outside the image and never blended) and
+    // slides the horizontal passes of rows r-1, r, r+1 down the strip; each
+    // output is the register path's blend of the same values, so the two
+    // paths give the same bits.
+    static __device__ bool run_ring(const Args &a, const Ctx &cx)
+    {
+        constexpr int R = kRingRows;
+        const int H = a.H, W = a.W, Wo = 2 * W;
+        const unsigned row_bytes = 4u * (unsigned)W;
+        if (cx.ring_stage < (R + 2) * row_bytes || (int64_t)a.P * H >= ((int64_t)1 << 32)) return false;
+        const unsigned ns = (unsigned)((H + R - 1) / R);
+        const int64_t items = (int64_t)a.P * ns;
+        WarpRing r;
+        r.init(cx, 0);
+        const int nw = cx.nthreads >> 5;
+        const int64_t gw = (int64_t)cx.block * nw + (cx.tid >> 5), GW = (int64_t)cx.grid * nw;
+        const unsigned dq = (unsigned)(GW / ns), dr = (unsigned)(GW % ns);
+        const int lane = lane_id();
+        const int c0 = 4 * lane;
+        const bool act = c0 < W;
+        ItemCursor fc, uc;   // the fill cursor runs S items ahead of the use cursor
+        fc.init(gw, ns);
+        uc = fc;
+        ring_stream(
+            r, gw, GW, items,
+            [&](int st, int64_t) {
+                const int r0 = (int)fc.s * R;
+                const int ylo = max(r0 - 1, 0), yhi = min(r0 + R + 1, H);
+                const unsigned bytes = (unsigned)(yhi - ylo) * row_bytes;   // rows are 16-byte multiples
+                r.expect(st, bytes);
+                r.copy(st, 0, a.x + ((uint64_t)fc.p * (unsigned)H + (unsigned)ylo) * W, bytes);
+                fc.step(dq, dr, ns);
+            },
+            [&](const unsigned char *stage, int64_t) {
+                const int r0 = (int)uc.s * R, r1 = min(r0 + R, H);
+                const int ylo = max(r0 - 1, 0), yhi = min(r0 + R + 1, H);
+                const unsigned char *base = stage + (act ? 4 * c0 : 0);
+                auto hrow = [&](int y, float h[8]) {
+                    y = min(max(y, ylo), yhi - 1);   // rows outside are never blended
+                    Raw q;
+                    q.q = *reinterpret_cast<const float4 *>(base + (unsigned)(y - ylo) * row_bytes);
+                    q.left = 0.f;
+                    q.right = 0.f;
+                    hpass(q, c0, W, h);
+                };
+                float *yp = a.y + ((int64_t)uc.p * (2 * H) + 2 * r0) * Wo + 2 * c0;
+                float hp[8], hc[8], hn[8];
+                hrow(r0 - 1, hp);
+                hrow(r0, hc);
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const int rr = r0 + i;
+                    hrow(rr + 1, hn);
+                    if (rr < r1) {
+                        float e[8], o[8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            e[k] = rr == 0 ? hc[k] : blend(hc[k], hp[k]);
+                            o[k] = rr == H - 1 ? hc[k] : blend(hc[k], hn[k]);
+                        }
+                        if (act) {
+                            float *ye = yp + (int64_t)(2 * i) * Wo;
+                            stcs4(ye, make_float4(e[0], e[1], e[2], e[3]));
+                            stcs4(ye + 4, make_float4(e[4], e[5], e[6], e[7]));
+                            stcs4(ye + Wo, make_float4(o[0], o[1], o[2], o[3]));
+                            stcs4(ye + Wo + 4, make_float4(o[4], o[5], o[6], o[7]));
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) hp[k] = hc[k], hc[k] = hn[k];
+                }
+                uc.step(dq, dr, ns);
+            });
+        r.finish();
+        return true;
+    }
+
     static __device__ void run_scalar(const Args &a, const Ctx &cx)
     {
         const int H = a.H, W = a.W, Ho = 2 * H, Wo = 2 * W;
@@ -166,10 +278,12 @@ struct BodyUpsample {
     static __device__ void run(const Args &a, const Ctx &cx)
     {
         if ((int64_t)a.P * a.H * a.W == 0) return;
-        if ((a.W & 3) == 0 && aligned16(a.x) && aligned16(a.y))
+        if ((a.W & 3) == 0 && aligned16(a.x) && aligned16(a.y)) {
+            if (a.W <= 128 && WarpRing::available(cx, 0) && run_ring(a, cx)) return;
             run_vec(a, cx);
-        else
+        } else {
             run_scalar(a, cx);
+        }
     }
 };
 
@@ -182,7 +296,8 @@ struct BodyMaxpool {
     static constexpr int kBarriers = 0;
     // ring path: a stage must hold the 9 input rows of a strip of 4 output
     // rows (rows of up to 128 floats)
-    static constexpr unsigned kRingMinBytes = 4096;
+    static constexpr bool kRingItem = true;
+    static constexpr unsigned kRingMinBytes = 4096;   // the stage: one item
 
     // strips of whole rows (W <= 128, 16-byte rows) arrive as one bulk copy
     static __host__ bool uses_ring(const Args &a)
@@ -273,23 +388,6 @@ struct BodyMaxpool {
     // depend on registers or warps.
     static constexpr int kRingRows = 4;   // output rows per ring work item
 
-    // (plane, strip) of a warp's items, advanced by the constant item stride
-    // without divisions.
-    struct Cursor {
-        unsigned p, s;
-        __device__ void init(int64_t it, unsigned ns)
-        {
-            p = (unsigned)(it / ns);
-            s = (unsigned)(it - (int64_t)p * ns);
-        }
-        __device__ void step(unsigned dq, unsigned dr, unsigned ns)
-        {
-            s += dr;
-            p += dq;
-            if (s >= ns) s -= ns, ++p;
-        }
-    };
-
     static __device__ bool run_ring(const Args &a, const Ctx &cx)
     {
         constexpr int R = kRingRows, NR = 2 * R + 1;
@@ -307,7 +405,7 @@ struct BodyMaxpool {
         const int c0 = 4 * lane;
         const bool act = c0 < W;
         const float ninf = -__int_as_float(0x7f800000);
-        Cursor fc, uc;   // the fill cursor runs S items ahead of the use cursor
+        ItemCursor fc, uc;   // the fill cursor runs S items ahead of the use cursor
         fc.init(gw, ns);
         uc = fc;
         ring_stream(

@@ -44,19 +44,38 @@ struct BodyOps {
     size_t (*smem)(int, const void *);
     size_t (*workspace)(const void *);
     int barriers;
-    bool (*ring)(const void *);   // will stream these arguments through a bulk-copy ring
-    unsigned ring_min;            // ...if each warp keeps at least this many bytes in flight
+    int (*ring)(const void *);    // ring kind for these arguments (RingKind below)
+    unsigned ring_min;            // stream ring: least bytes in flight per warp worth a ring;
+                                  // item ring: the stage size (one work item)
     const char *name;
 };
 
-// Bodies with a ring path declare `static bool uses_ring(const Args &)`.
+// How a body uses a bulk-copy ring: not at all; streaming whole tiles of a
+// flat array (any stage size, a share of the SM's bytes in flight); or one
+// work item per stage (a fixed stage of ring_min bytes, two per warp).
+enum RingKind { kRingNone = 0, kRingStream = 1, kRingItem = 2 };
+
+// Bodies with a ring path declare `static bool uses_ring(const Args &)`;
+// those that take one work item per stage also declare kRingItem = true.
+template <class B, class = void>
+struct RingItem {
+    static constexpr bool value = false;
+};
+template <class B>
+struct RingItem<B, std::void_t<decltype(B::kRingItem)>> {
+    static constexpr bool value = B::kRingItem;
+};
 template <class B, class = void>
 struct RingTrait {
-    static bool uses(const void *) { return false; }
+    static int uses(const void *) { return kRingNone; }
 };
 template <class B>
 struct RingTrait<B, std::void_t<decltype(B::uses_ring(std::declval<const typename B::Args &>()))>> {
-    static bool uses(const void *p) { return B::uses_ring(*static_cast<const typename B::Args *>(p)); }
+    static int uses(const void *p)
+    {
+        if (!B::uses_ring(*static_cast<const typename B::Args *>(p))) return kRingNone;
+        return RingItem<B>::value ? kRingItem : kRingStream;
+    }
 };
 template <class B, class = void>
 struct RingMin {
@@ -311,28 +330,46 @@ void ring_geom(double F, unsigned *stage, int *stages)
 }
 
 // The ring decision for `b` resident blocks of a block whose intervals have
-// warps[i] warps, ring[i] (a body that can stream through a ring) and
-// ring_min[i] (the bytes in flight per warp below which it is better off on
-// register loads): intervals whose minimum the SM's share misses drop their
-// ring and the share is recomputed over the rest.  Returns the geometry and
-// which intervals keep a ring.
-void ring_choice(int n, const int *warps, const bool *ring, const unsigned *ring_min, int b, bool *use,
-                 unsigned *stage, int *stages)
+// warps[i] warps, ring kind kind[i] and ring_min[i].  Item rings (when
+// `items`) get their fixed geometry: stages of ring_min[i] bytes, two per
+// warp.  Stream rings share about 40 KB in flight per SM over their warps
+// (the bf16 stream's optimum); intervals whose minimum the SM's share misses
+// drop their ring and the share is recomputed over the rest.  Returns which
+// intervals keep a ring and each one's stage bytes and stages.
+constexpr int kItemStages = 2;
+void ring_choice(int n, const int *warps, const int *kind, const unsigned *ring_min, int b, bool items,
+                 bool *use, unsigned *stage, int *stages)
 {
-    for (int i = 0; i < n; ++i) use[i] = ring[i] && b > 0;
+    for (int i = 0; i < n; ++i) {
+        use[i] = b > 0 && (kind[i] == kRingStream || (kind[i] == kRingItem && items));
+        stage[i] = 0;
+        stages[i] = 0;
+    }
     double F = 0.0;
     for (bool changed = true; changed;) {
         changed = false;
         int w = 0;
         for (int i = 0; i < n; ++i)
-            if (use[i]) w += warps[i];
+            if (use[i] && kind[i] == kRingStream) w += warps[i];
         F = w > 0 ? 40960.0 / ((double)b * w) : 0.0;
         for (int i = 0; i < n; ++i)
-            if (use[i] && F < ring_min[i]) use[i] = false, changed = true;
+            if (use[i] && kind[i] == kRingStream && F < ring_min[i]) use[i] = false, changed = true;
     }
-    ring_geom(F, stage, stages);
-    if (*stages == 0)
-        for (int i = 0; i < n; ++i) use[i] = false;
+    unsigned sB = 0;
+    int sS = 0;
+    ring_geom(F, &sB, &sS);
+    for (int i = 0; i < n; ++i) {
+        if (!use[i]) continue;
+        if (kind[i] == kRingItem) {
+            stage[i] = (ring_min[i] + 127u) / 128u * 128u;
+            stages[i] = kItemStages;
+        } else if (sS > 0) {
+            stage[i] = sB;
+            stages[i] = sS;
+        } else {
+            use[i] = false;
+        }
+    }
 }
 
 // Shared-memory layout, ring geometry and grid of one launch.
@@ -351,7 +388,7 @@ struct LaunchPlan {
 // explicit grid `want`, no more than it spreads over the SMs); the grid is
 // `want` or blocks per SM x SMs.
 hf_status plan_launch(const void *func, int d0, int n, const int *threads, const size_t *base,
-                      const bool *ring, const unsigned *ring_min, int want, LaunchPlan *out)
+                      const int *ring, const unsigned *ring_min, int want, LaunchPlan *out)
 {
     hf_device_limits lim;
     hf_status s = limits(&lim);
@@ -372,36 +409,36 @@ hf_status plan_launch(const void *func, int d0, int n, const int *threads, const
         return fail(HF_ERR_REGS, "block of %d threads with %zu B shared memory cannot be resident", d0,
                     base_total);
     if (want > 0) bmax = std::max(1, std::min(bmax, (want + lim.sm_count - 1) / lim.sm_count));
-    for (int b = bmax; b >= 0; --b) {
-        // b == 0: the last resort, no rings at the largest block count.
-        // Intervals whose body wants more in flight per warp than the SM's
-        // share gives drop their ring (register loads), and the share is
-        // recomputed over the rest.
-        bool use[HF_MAX_INTERVALS];
-        int warps[HF_MAX_INTERVALS];
-        for (int i = 0; i < n; ++i) warps[i] = threads[i] / 32;
-        unsigned stage = 0;
-        int stages = 0;
-        ring_choice(n, warps, ring, ring_min, b, use, &stage, &stages);
-        size_t off = 0;
-        for (int i = 0; i < n; ++i) {
-            out->off[i] = (unsigned)off;
-            const bool r = use[i] && stages > 0;
-            out->ring_stage[i] = r ? stage : 0;
-            out->ring_stages[i] = r ? stages : 0;
-            off += align128(align128(base[i]) + (r ? ring_bytes(threads[i], stage, stages) : 0));
+    for (int b = bmax; b >= 0; --b)
+        for (int items = 1; items >= 0; --items) {
+            // b == 0: the last resort, no rings at the largest block count.
+            // Item rings that do not fit go before the block count drops;
+            // stream intervals whose body wants more in flight per warp than
+            // the SM's share gives drop their ring (register loads).
+            bool use[HF_MAX_INTERVALS];
+            int warps[HF_MAX_INTERVALS], stages[HF_MAX_INTERVALS];
+            unsigned stage[HF_MAX_INTERVALS];
+            for (int i = 0; i < n; ++i) warps[i] = threads[i] / 32;
+            ring_choice(n, warps, ring, ring_min, b, items != 0, use, stage, stages);
+            size_t off = 0;
+            for (int i = 0; i < n; ++i) {
+                out->off[i] = (unsigned)off;
+                const bool r = use[i] && stages[i] > 0;
+                out->ring_stage[i] = r ? stage[i] : 0;
+                out->ring_stages[i] = r ? stages[i] : 0;
+                off += align128(align128(base[i]) + (r ? ring_bytes(threads[i], stage[i], stages[i]) : 0));
+            }
+            if (off > (size_t)lim.smem_per_block_optin) continue;
+            int got = 0;
+            s = occ_blocks(func, d0, off, &got);
+            if (s) return s;
+            if (got >= std::max(b, 1)) {
+                out->smem = (unsigned)off;
+                out->bps = b > 0 ? b : bmax;
+                out->grid = want > 0 ? want : out->bps * lim.sm_count;
+                return HF_OK;
+            }
         }
-        if (off > (size_t)lim.smem_per_block_optin) continue;
-        int got = 0;
-        s = occ_blocks(func, d0, off, &got);
-        if (s) return s;
-        if (got >= std::max(b, 1)) {
-            out->smem = (unsigned)off;
-            out->bps = b > 0 ? b : bmax;
-            out->grid = want > 0 ? want : out->bps * lim.sm_count;
-            return HF_OK;
-        }
-    }
     return fail(HF_ERR_REGS, "no resident configuration for a block of %d threads", d0);
 }
 
@@ -414,18 +451,18 @@ hf_status plan_launch(const void *func, int d0, int n, const int *threads, const
 namespace hf {
 void interval_smem_at(const int *ids, const void *const *args, const int *threads, int b, double *out)
 {
-    bool ring[2], use[2];
-    unsigned mins[2], stage = 0;
-    int warps[2], stages = 0;
+    bool use[2];
+    unsigned mins[2], stage[2];
+    int kind[2], warps[2], stages[2];
     for (int i = 0; i < 2; ++i) {
-        ring[i] = valid_body(ids[i]) && body_ops(ids[i]).ring(args[i]);
+        kind[i] = valid_body(ids[i]) ? body_ops(ids[i]).ring(args[i]) : kRingNone;
         mins[i] = valid_body(ids[i]) ? body_ops(ids[i]).ring_min : 0u;
         warps[i] = threads[i] / 32;
     }
-    ring_choice(2, warps, ring, mins, b, use, &stage, &stages);
+    ring_choice(2, warps, kind, mins, b, true, use, stage, stages);
     for (int i = 0; i < 2; ++i) {
         const double base = valid_body(ids[i]) ? (double)body_ops(ids[i]).smem(threads[i], args[i]) : 0.0;
-        out[i] = base + (use[i] && stages > 0 ? (double)ring_bytes(threads[i], stage, stages) : 0.0);
+        out[i] = base + (use[i] && stages[i] > 0 ? (double)ring_bytes(threads[i], stage[i], stages[i]) : 0.0);
     }
 }
 } // namespace hf
@@ -435,7 +472,7 @@ hf_status single_plan(const hf_kernel_t *k, const void *args, int threads, int w
 {
     const SingleEntry *e = find_single(k->body);
     const size_t base = body_ops(k->body).smem(threads, args);
-    const bool ring = body_ops(k->body).ring(args);
+    const int ring = body_ops(k->body).ring(args);
     const unsigned ring_min = body_ops(k->body).ring_min;
     return plan_launch(e->func, threads, 1, &threads, &base, &ring, &ring_min, want, plan);
 }
@@ -457,23 +494,27 @@ hf_status nway_params(const hf_fused_t *f, const void *const *args, int want, Nw
     p->n_int = f->n_int;
     int w = 0;
     size_t base[HF_MAX_INTERVALS];
-    bool ring[HF_MAX_INTERVALS];
+    int ring[HF_MAX_INTERVALS];
     unsigned ring_min[HF_MAX_INTERVALS];
     for (int i = 0; i < f->n_int; ++i) {
         p->warp_begin[i] = w;
         w += f->int_threads[i] / 32;
         base[i] = 0;
-        ring[i] = false;
+        ring[i] = kRingNone;
         ring_min[i] = 0;
+        // kernels sharing an interval share its ring: item geometry (the
+        // largest item) when any of them takes items, a stream share else
+        unsigned item_min = 0, stream_min = 0;
         for (int j = 0; j < f->n; ++j)
             if (f->sched_int[j] == i) {
                 const BodyOps &o = body_ops(f->sched_body[j]);
                 base[i] = std::max(base[i], o.smem(f->int_threads[i], args[j]));
-                if (o.ring(args[j])) {
-                    ring[i] = true;
-                    ring_min[i] = std::max(ring_min[i], o.ring_min);
-                }
+                const int k = o.ring(args[j]);
+                if (k == kRingItem) item_min = std::max(item_min, o.ring_min);
+                if (k == kRingStream) stream_min = std::max(stream_min, o.ring_min);
             }
+        if (item_min) ring[i] = kRingItem, ring_min[i] = item_min;
+        else if (stream_min) ring[i] = kRingStream, ring_min[i] = stream_min;
     }
     p->warp_begin[f->n_int] = w;
     for (int i = 0; i < f->n_int; ++i)
@@ -520,7 +561,7 @@ hf_status pair_plan(const hf_fused_t *f, const void *const *uargs, int want, Lau
     const int threads[2] = {f->n_low, f->n_high};
     const size_t base[2] = {body_ops(f->body_low).smem(f->n_low, uargs[0]),
                             body_ops(f->body_high).smem(f->n_high, uargs[1])};
-    const bool ring[2] = {body_ops(f->body_low).ring(uargs[0]), body_ops(f->body_high).ring(uargs[1])};
+    const int ring[2] = {body_ops(f->body_low).ring(uargs[0]), body_ops(f->body_high).ring(uargs[1])};
     const unsigned ring_min[2] = {body_ops(f->body_low).ring_min, body_ops(f->body_high).ring_min};
     return plan_launch(f->inst->func, f->d0, 2, threads, base, ring, ring_min, want, plan);
 }
@@ -565,9 +606,13 @@ hf_status hf_ring_plan(int n, const int *warps, const int *ring, const unsigned 
     if (n < 1 || n > HF_MAX_INTERVALS || !warps || !ring || !min_bytes || !stage || !stages || !uses ||
         blocks_per_sm < 1)
         return fail(HF_ERR_INVALID, "bad ring-plan arguments");
-    bool r[HF_MAX_INTERVALS], use[HF_MAX_INTERVALS];
-    for (int i = 0; i < n; ++i) r[i] = ring[i] != 0;
-    ring_choice(n, warps, r, min_bytes, blocks_per_sm, use, stage, stages);
+    int kind[HF_MAX_INTERVALS];
+    bool use[HF_MAX_INTERVALS];
+    for (int i = 0; i < n; ++i) {
+        if (ring[i] < kRingNone || ring[i] > kRingItem) return fail(HF_ERR_INVALID, "bad ring kind");
+        kind[i] = ring[i];
+    }
+    ring_choice(n, warps, kind, min_bytes, blocks_per_sm, true, use, stage, stages);
     for (int i = 0; i < n; ++i) uses[i] = use[i] ? 1 : 0;
     return HF_OK;
 }

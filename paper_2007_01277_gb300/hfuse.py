@@ -708,11 +708,14 @@ def hf_autotune(a, b, args, d0=512, mode=TUNE_EXHAUSTIVE, reps=5, flush_l2=False
     return best.as_dict()
 
 
+RING_NONE, RING_STREAM, RING_ITEM = 0, 1, 2
+
+
 def hf_ring_plan(warps, ring, min_bytes, blocks_per_sm):
-    """(stage bytes, stages, [uses]) of the launch planner's ring decision."""
+    """([stage bytes], [stages], [uses]) per interval of the launch planner's
+    ring decision; ring[i] is RING_NONE, RING_STREAM or RING_ITEM."""
     n = len(warps)
-    st, ns, uses = ctypes.c_uint(), _i32(), (_i32 * n)()
+    st, ns, uses = (ctypes.c_uint * n)(), (_i32 * n)(), (_i32 * n)()
     _check("hf_ring_plan", lib.hf_ring_plan(n, (_i32 * n)(*warps), (_i32 * n)(*[int(r) for r in ring]),
-                                            (ctypes.c_uint * n)(*min_bytes), blocks_per_sm,
-                                            ctypes.byref(st), ctypes.byref(ns), uses))
-    return st.value, ns.value, list(uses)
+                                            (ctypes.c_uint * n)(*min_bytes), blocks_per_sm, st, ns, uses))
+    return list(st), list(ns), list(uses)

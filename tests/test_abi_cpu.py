@@ -148,26 +148,34 @@ def test_template_features_hand_example(H):
 
 
 def test_ring_plan_geometry(H):
-    """About 40 KB in flight per SM over the SM's ring warps, in stages of 1,
-    2 or 4 KB, 2 to 4 per warp; below a body's minimum share it drops its
-    ring and the share is recomputed over the rest."""
+    """Stream rings: about 40 KB in flight per SM over the SM's stream-ring
+    warps, in stages of 1, 2 or 4 KB, 2 to 4 per warp; below a body's
+    minimum share it drops its ring and the share is recomputed over the
+    rest.  Item rings: two stages of the item size, outside that share."""
+    S, I = H.RING_STREAM, H.RING_ITEM
     # 8 ring warps: 5 KB per warp -> 4 KB stages, 2 of them
-    assert H.hf_ring_plan([8], [1], [1024], 1) == (4096, 2, [1])
+    assert H.hf_ring_plan([8], [S], [1024], 1) == ([4096], [2], [1])
     # 4 warps: 10 KB per warp -> 4 KB stages, 1 + round(2.5) = 4 (the cap)
-    assert H.hf_ring_plan([4], [1], [1024], 1) == (4096, 4, [1])
+    assert H.hf_ring_plan([4], [S], [1024], 1) == ([4096], [4], [1])
     # 2 warps: 20 KB per warp -> still 4 stages of 4 KB
-    assert H.hf_ring_plan([2], [1], [1024], 1) == (4096, 4, [1])
+    assert H.hf_ring_plan([2], [S], [1024], 1) == ([4096], [4], [1])
     # 32 warps: 1.25 KB -> 1 KB stages, 2 of them
-    assert H.hf_ring_plan([16], [1], [1024], 2) == (1024, 2, [1])
+    assert H.hf_ring_plan([16], [S], [1024], 2) == ([1024], [2], [1])
     # 64 warps: 640 B per warp, below 1 KB -> register loads
-    assert H.hf_ring_plan([16], [1], [1024], 4) == (0, 0, [0])
+    assert H.hf_ring_plan([16], [S], [1024], 4) == ([0], [0], [0])
     # two ring intervals of 16 warps: 1.25 KB each misses the second one's
     # 2 KB minimum; it drops out and the first gets 2.5 KB -> 2 KB stages
-    assert H.hf_ring_plan([16, 16], [1, 1], [1024, 2048], 1) == (2048, 2, [1, 0])
+    assert H.hf_ring_plan([16, 16], [S, S], [1024, 2048], 1) == ([2048, 0], [2, 0], [1, 0])
     # intervals without a ring never get one
-    assert H.hf_ring_plan([4, 28], [0, 1], [1024, 1024], 1) == (1024, 2, [0, 1])
+    assert H.hf_ring_plan([4, 28], [0, S], [1024, 1024], 1) == ([0, 1024], [0, 2], [0, 1])
+    # an item interval keeps two 4 KB stages whatever the warps and does not
+    # count against the stream share: 8 stream warps still get 5 KB each
+    assert H.hf_ring_plan([16, 8], [I, S], [4096, 1024], 2) == ([4096, 2048], [2, 2], [1, 1])
+    assert H.hf_ring_plan([4, 8], [I, S], [4000, 1024], 1) == ([4096, 4096], [2, 2], [1, 1])
     with pytest.raises(H.HFError):
-        H.hf_ring_plan([4], [1], [1024], 0)
+        H.hf_ring_plan([4], [S], [1024], 0)
+    with pytest.raises(H.HFError):
+        H.hf_ring_plan([4], [3], [1024], 1)
 
 
 def test_pair_features_reduce_to_template_features(H):
