@@ -43,7 +43,15 @@ struct BodyBn {
         return counters_bytes(a) + (size_t)a.C * tiles_per_channel(a) * sizeof(float2);
     }
     static constexpr size_t kPoolBytes = 16;   // the block's tile pool counter
-    static __host__ size_t smem_bytes(int /*nthreads*/, const Args &) { return kPoolBytes; }
+    static constexpr size_t kRingOffset = 128;   // the ring follows the pool counter
+    // ring path: one stage per tile (its <= 3 contiguous runs, HW >= 1024)
+    static constexpr bool kRingItem = true;
+    static constexpr unsigned kRingMinBytes = kTile * sizeof(float);
+    static __host__ bool uses_ring(const Args &a)
+    {
+        return a.C > 0 && a.N > 0 && a.HW >= 1024 && (a.HW & 3) == 0 && aligned16(a.x);
+    }
+    static __host__ size_t smem_bytes(int /*nthreads*/, const Args &) { return kRingOffset; }
     static __host__ hf_status validate(const Args &a)
     {
         if (a.N < 0 || a.C < 0 || a.HW < 0) return HF_ERR_INVALID;
@@ -55,17 +63,15 @@ struct BodyBn {
         return HF_OK;
     }
 
-    template <int VEC>
-    static __device__ __forceinline__ void tile_sums(const Args &a, int c, int64_t t, float K,
-                                                     float &s1, float &s2)
+    // The tile's FP32 sums of d = x - K and d*d, in the one order every
+    // path uses: lane l takes the VEC values at tile offsets VEC*l + 32*VEC*k
+    // for k = 0, 1, ... (values past the channel's end read as K, so d = 0),
+    // in batches of 8 steps whose values get(k) returns -- the batch's
+    // loads are all issued before its arithmetic; four per-lane sums (two
+    // packed pairs for VEC = 4), then their sum and a warp butterfly.
+    template <int VEC, class Get>
+    static __device__ __forceinline__ void accumulate(Get get, float K, float &s1, float &s2)
     {
-        const int64_t M = (int64_t)a.N * a.HW;
-        const int lane = lane_id();
-        const int64_t j0 = t * kTile + (int64_t)VEC * lane;
-        // (n, hw) of this lane's first value; later values advance by 32*VEC.
-        int n = (int)(j0 / a.HW);
-        int hw = (int)(j0 - (int64_t)n * a.HW);
-        const int64_t jend = (t + 1) * kTile < M ? (t + 1) * kTile : M;
         float p1[VEC], p2[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) p1[v] = 0.f, p2[v] = 0.f;
@@ -75,30 +81,11 @@ struct BodyBn {
         const unsigned long long KK = f2pack(K, K);
         constexpr int kSteps = kTile / (32 * VEC);
         constexpr int kBatch = 8;
-        int64_t j = j0;
 #pragma unroll 1
         for (int s = 0; s < kSteps; s += kBatch) {
             float vals[kBatch][VEC];
 #pragma unroll
-            for (int b = 0; b < kBatch; ++b) {
-                const bool ok = (s + b < kSteps) && (j < jend);
-                const float *p = a.x + ((int64_t)n * a.C + c) * a.HW + hw;
-                if (VEC == 4) {
-                    float4 q = ok ? ldcs4(p) : make_float4(K, K, K, K);
-                    vals[b][0] = q.x;
-                    if (VEC > 1) vals[b][1 % VEC] = q.y;
-                    if (VEC > 2) vals[b][2 % VEC] = q.z;
-                    if (VEC > 3) vals[b][3 % VEC] = q.w;
-                } else {
-                    vals[b][0] = ok ? __ldcs(p) : K;
-                }
-                j += 32 * VEC;
-                hw += 32 * VEC;
-                while (hw >= a.HW) {
-                    hw -= a.HW;
-                    ++n;
-                }
-            }
+            for (int b = 0; b < kBatch; ++b) get(s + b, vals[b]);
             if (VEC == 4) {
 #pragma unroll
                 for (int b = 0; b < kBatch; ++b) {
@@ -138,6 +125,43 @@ struct BodyBn {
             s1 = __fadd_rn(s1, __shfl_xor_sync(0xffffffffu, s1, m));
             s2 = __fadd_rn(s2, __shfl_xor_sync(0xffffffffu, s2, m));
         }
+    }
+
+    // Register path: the values straight from global memory (streaming
+    // loads), the lane's (n, hw) position advanced step by step.
+    template <int VEC>
+    static __device__ __forceinline__ void tile_sums(const Args &a, int c, int64_t t, float K,
+                                                     float &s1, float &s2)
+    {
+        const int64_t M = (int64_t)a.N * a.HW;
+        const int lane = lane_id();
+        const int64_t j0 = t * kTile + (int64_t)VEC * lane;
+        // (n, hw) of this lane's first value; later values advance by 32*VEC.
+        int n = (int)(j0 / a.HW);
+        int hw = (int)(j0 - (int64_t)n * a.HW);
+        const int64_t jend = (t + 1) * kTile < M ? (t + 1) * kTile : M;
+        int64_t j = j0;
+        accumulate<VEC>(
+            [&](int, float(&v)[VEC]) {
+                const bool ok = j < jend;
+                const float *p = a.x + ((int64_t)n * a.C + c) * a.HW + hw;
+                if (VEC == 4) {
+                    const float4 q = ok ? ldcs4(p) : make_float4(K, K, K, K);
+                    v[0] = q.x;
+                    v[1 % VEC] = q.y;
+                    v[2 % VEC] = q.z;
+                    v[3 % VEC] = q.w;
+                } else {
+                    v[0] = ok ? __ldcs(p) : K;
+                }
+                j += 32 * VEC;
+                hw += 32 * VEC;
+                while (hw >= a.HW) {
+                    hw -= a.HW;
+                    ++n;
+                }
+            },
+            K, s1, s2);
     }
 
     // Double-float sums: hi + lo, |lo| <= ulp(hi)/2, about 48 significant
@@ -271,6 +295,117 @@ struct BodyBn {
         }
     }
 
+    // Ring path.  The same tiles, taken from the block's pool two ahead:
+    // lane 0 copies each tile's runs of the channel (a tile crosses at most
+    // two image boundaries when HW >= 1024) into a stage of the warp's ring,
+    // contiguous in the tile's order, and the lanes read their values from
+    // shared memory in the order of accumulate(), so the sums -- and with
+    // them the results -- are those of the register path, bit for bit.
+    // Returns false (nothing done) when the launch's ring does not fit.
+    static __device__ bool run_ring(const Args &a, const Ctx &cx, unsigned *pool)
+    {
+        const int64_t T64 = tiles_per_channel(a);
+        const int64_t M = (int64_t)a.N * a.HW;
+        // 32-bit tile arithmetic (fewer registers); larger tensors take the
+        // register path
+        if (!pool || cx.ring_stages != 2 || cx.ring_stage < kRingMinBytes || (int64_t)a.C * T64 >= ((int64_t)1 << 31) ||
+            M >= ((int64_t)1 << 31) || !WarpRing::available(cx, kRingOffset))
+            return false;
+        const unsigned T = (unsigned)T64;
+        const unsigned ntiles = (unsigned)a.C * T;
+        unsigned *cnt = reinterpret_cast<unsigned *>(a.workspace);
+        float2 *part = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(a.workspace) +
+                                                  counters_bytes(a));
+        const int lane = lane_id();
+        const unsigned G = (unsigned)cx.grid, b = (unsigned)cx.block;
+        const unsigned q = ntiles / G, rem = ntiles % G;
+        const unsigned bstart = b * q + (b < rem ? b : rem);
+        const unsigned bend = bstart + q + (b < rem ? 1u : 0u);
+        WarpRing r;
+        r.init(cx, kRingOffset);
+        // lane 0: the next tile of the block's range (ntiles when done)
+        auto grab = [&]() -> unsigned {
+            const unsigned tl = bstart + atomicAdd(pool, 1u);
+            return tl < bend ? tl : ntiles;
+        };
+        // lane 0: the tile's runs into stage st
+        auto fill = [&](int st, unsigned tile) {
+            const unsigned c = tile / T, t = tile - c * T;
+            int j = (int)(t * kTile);
+            const int jend = min(j + kTile, (int)M);
+            r.expect(st, (unsigned)(4 * (jend - j)));
+            int n = j / a.HW;
+            int hw = j - n * a.HW;
+            const int j0 = j;
+            while (j < jend) {
+                const int len = min(a.HW - hw, jend - j);
+                r.copy(st, (unsigned)(4 * (j - j0)), a.x + ((int64_t)n * a.C + c) * a.HW + hw, (unsigned)(4 * len));
+                j += len;
+                hw = 0;
+                ++n;
+            }
+        };
+        unsigned tl0 = ntiles, tl1 = ntiles;   // the stages' tiles (lane 0)
+        if (lane == 0) {
+            tl0 = grab();
+            if (tl0 < ntiles) fill(0, tl0);
+            tl1 = grab();
+            if (tl1 < ntiles) fill(1, tl1);
+        }
+        int s = 0;
+        unsigned ph = 0;
+        for (;;) {
+            // tiles are grabbed in increasing order: once one is past the
+            // range, so is every later one, and no copy is in flight
+            const unsigned tile = __shfl_sync(0xffffffffu, s ? tl1 : tl0, 0);
+            if (tile >= ntiles) break;
+            if (!r.wait(s, ph)) {
+                if (lane == 0 && cx.err) atomicOr(cx.err, kErrWaitExpired);
+                const unsigned other = __shfl_sync(0xffffffffu, s ? tl0 : tl1, 0);
+                if (other < ntiles) r.wait(s ^ 1, s ? ph ^ 1u : ph);
+                break;
+            }
+            const int c = (int)(tile / T);
+            const int tt = (int)(tile - (unsigned)c * T);
+            const float K = __ldg(a.x + (int64_t)c * a.HW);
+            const int valid = min(kTile, (int)M - tt * kTile);   // values of this tile
+            const float4 *st4 = reinterpret_cast<const float4 *>(r.stage(s));
+            float s1, s2;
+            accumulate<4>(
+                [&](int k, float(&v)[4]) {
+                    const int off = 4 * lane + 128 * k;   // value offset within the tile
+                    const float4 x4 = off < valid ? st4[off >> 2] : make_float4(K, K, K, K);
+                    v[0] = x4.x;
+                    v[1] = x4.y;
+                    v[2] = x4.z;
+                    v[3] = x4.w;
+                },
+                K, s1, s2);
+            __syncwarp();
+            if (lane == 0) {
+                r.refill_fence();
+                const unsigned nx = grab();
+                if (nx < ntiles) fill(s, nx);
+                if (s) tl1 = nx;
+                else tl0 = nx;
+            }
+            bool last = false;
+            if (lane == 0) {
+                part[tile] = make_float2(s1, s2);
+                last = atom_add_acq_rel_gpu(cnt + c, 1u) == (unsigned)(T - 1);
+            }
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __syncwarp();
+                finalize(a, c, (int64_t)T, K, part, cnt);
+            }
+            s ^= 1;
+            if (s == 0) ph ^= 1u;
+        }
+        r.finish();
+        return true;
+    }
+
     static __device__ void run(const Args &a, const Ctx &cx)
     {
         if (a.C <= 0) return;
@@ -280,10 +415,12 @@ struct BodyBn {
             if (cx.tid == 0) *pool = 0u;
             interval_sync(cx);
         }
-        if ((a.HW & 3) == 0 && aligned16(a.x))
+        if ((a.HW & 3) == 0 && aligned16(a.x)) {
+            if (a.HW >= 1024 && run_ring(a, cx, pool)) return;
             run_vec<4>(a, cx, pool);
-        else
+        } else {
             run_vec<1>(a, cx, pool);
+        }
     }
 };
 
