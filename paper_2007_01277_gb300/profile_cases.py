@@ -128,7 +128,7 @@ def main():
     ap.add_argument("--bps", type=int, default=0)
     ap.add_argument("--threads", type=int, default=256)
     ap.add_argument("--scale", type=float, default=1.0)
-    ap.add_argument("--plan", default="3,3,2,1,3,1,0,2;128,288,352,256;48")
+    ap.add_argument("--plan", default="2,3,2,2,1,3,0,1;384,128,288,224;64")
     a = ap.parse_args()
     dev = torch.device("cuda:0")
     parts = build(a.case, a.scale, dev)
