@@ -497,6 +497,18 @@ struct BodyIm2col {
     using Args = hf_im2col3_args;
     static constexpr int kId = HF_BODY_IM2COL3;
     static constexpr int kBarriers = 0;
+    // ring path: a stage holds an item's 14 rows and its two halo rows
+    // (rows of up to 64 floats)
+    static constexpr int kRingRows = 14;
+    static constexpr bool kRingItem = true;
+    static constexpr unsigned kRingMinBytes = 4096;   // the stage: one item
+
+    // chunks of whole rows (W <= 64, 16-byte rows) arrive as one bulk copy
+    static __host__ bool uses_ring(const Args &a)
+    {
+        return (int64_t)a.N * a.C * a.H * a.W > 0 && (a.W & 3) == 0 && a.W <= 64 && aligned16(a.x) &&
+               aligned16(a.col);
+    }
 
     static __host__ size_t workspace_bytes(const Args &) { return 0; }
     static __host__ size_t smem_bytes(int, const Args &) { return 0; }
@@ -592,6 +604,78 @@ struct BodyIm2col {
         }
     }
 
+    // Ring path.  Work item = (plane, chunk of R = 14 rows); the chunk and
+    // its halo rows, [max(r0-1, 0), min(r0+R+1, H)), are contiguous and
+    // arrive in one bulk copy in a stage of the warp's ring.  As in the
+    // register path each half-warp takes half of the chunk and lane l of a
+    // half the columns 4l..4l+3, sliding three rows (from shared memory,
+    // zero outside the image) and writing the nine shifted copies per row.
+    static __device__ bool run_ring(const Args &a, const Ctx &cx)
+    {
+        constexpr int R = kRingRows, RH = R / 2;
+        const int H = a.H, W = a.W;
+        const int64_t HW = (int64_t)H * W;
+        const unsigned row_bytes = 4u * (unsigned)W;
+        const int64_t planes = (int64_t)a.N * a.C;
+        if (cx.ring_stage < (R + 2) * row_bytes || planes * H >= ((int64_t)1 << 32)) return false;
+        const unsigned ns = (unsigned)((H + R - 1) / R);
+        const int64_t items = planes * ns;
+        WarpRing r;
+        r.init(cx, 0);
+        const int nw = cx.nthreads >> 5;
+        const int64_t gw = (int64_t)cx.block * nw + (cx.tid >> 5), GW = (int64_t)cx.grid * nw;
+        const unsigned dq = (unsigned)(GW / ns), dr = (unsigned)(GW % ns);
+        const int lane = lane_id();
+        const int half = lane >> 4;
+        const int c0 = 4 * (lane & 15);
+        const bool act = c0 < W;
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        ItemCursor fc, uc;   // the fill cursor runs S items ahead of the use cursor
+        fc.init(gw, ns);
+        uc = fc;
+        ring_stream(
+            r, gw, GW, items,
+            [&](int st, int64_t) {
+                const int r0 = (int)fc.s * R;
+                const int ylo = max(r0 - 1, 0), yhi = min(r0 + R + 1, H);
+                const unsigned bytes = (unsigned)(yhi - ylo) * row_bytes;   // rows are 16-byte multiples
+                r.expect(st, bytes);
+                r.copy(st, 0, a.x + ((uint64_t)fc.p * (unsigned)H + (unsigned)ylo) * W, bytes);
+                fc.step(dq, dr, ns);
+            },
+            [&](const unsigned char *stage, int64_t) {
+                const int r0 = (int)uc.s * R;
+                const int ylo = max(r0 - 1, 0), yhi = min(r0 + R + 1, H);
+                const unsigned char *base = stage + (act ? 4 * c0 : 0);
+                auto ld = [&](int y) {
+                    const int yc = min(max(y, ylo), yhi - 1);   // an in-stage row
+                    const float4 q = *reinterpret_cast<const float4 *>(base + (unsigned)(yc - ylo) * row_bytes);
+                    return (act && y >= 0 && y < H) ? q : zero;
+                };
+                const unsigned n = uc.p / (unsigned)a.C, c = uc.p - n * (unsigned)a.C;
+                float *cp = a.col + ((int64_t)n * a.C * 9 + (int64_t)c * 9) * HW;
+                const int oyb = r0 + half * RH, oye = min(oyb + RH, H);
+                Row up = halo(ld(oyb - 1), c0, W);
+                Row mid = halo(ld(oyb), c0, W);
+#pragma unroll
+                for (int i = 0; i < RH; ++i) {
+                    const int oy = oyb + i;
+                    Row dn = halo(ld(oy + 1), c0, W);
+                    if (act && oy < oye) {
+                        float *o = cp + (int64_t)oy * W + c0;
+                        emit(up, o, HW);
+                        emit(mid, o + 3 * HW, HW);
+                        emit(dn, o + 6 * HW, HW);
+                    }
+                    up = mid;
+                    mid = dn;
+                }
+                uc.step(dq, dr, ns);
+            });
+        r.finish();
+        return true;
+    }
+
     static __device__ void run_scalar(const Args &a, const Ctx &cx)
     {
         const int H = a.H, W = a.W;
@@ -614,10 +698,12 @@ struct BodyIm2col {
     static __device__ void run(const Args &a, const Ctx &cx)
     {
         if ((int64_t)a.N * a.C * a.H * a.W == 0) return;
-        if ((a.W & 3) == 0 && a.W <= 64 && aligned16(a.x) && aligned16(a.col))
+        if ((a.W & 3) == 0 && a.W <= 64 && aligned16(a.x) && aligned16(a.col)) {
+            if (WarpRing::available(cx, 0) && run_ring(a, cx)) return;
             run_vec(a, cx);
-        else
+        } else {
             run_scalar(a, cx);
+        }
     }
 };
 
