@@ -43,7 +43,10 @@ struct BodyBn {
         return counters_bytes(a) + (size_t)a.C * tiles_per_channel(a) * sizeof(float2);
     }
     static constexpr size_t kPoolBytes = 16;   // the block's tile pool counter
-    static constexpr size_t kRingOffset = 128;   // the ring follows the pool counter
+    // then kSlots per-channel tile counters of the block (block counting)
+    static constexpr int kSlots = 24;
+    static constexpr size_t kCountBytes = kPoolBytes + kSlots * sizeof(unsigned);
+    static constexpr size_t kRingOffset = 128;   // the ring follows the counters
     // ring path: one stage per tile (its <= 3 contiguous runs, HW >= 1024)
     static constexpr bool kRingItem = true;
     static constexpr unsigned kRingMinBytes = kTile * sizeof(float);
@@ -227,6 +230,50 @@ struct BodyBn {
         }
     }
 
+    // Counting finished tiles.  A channel is complete when all its T tiles
+    // are counted; the warp whose count completes it runs the combine.
+    // Per tile, a GPU-scope acquire-release atomic (its fence waits for the
+    // warp's memory operations, the top stall of a warp that has no other
+    // warps to hide it behind) -- unless the block counts first: its range
+    // of tiles covers channels c_lo..c_lo+k (k < kSlots), each warp adds
+    // its finished tile to the channel's counter in shared memory
+    // (acquire-release at CTA scope) and the warp that completes the
+    // block's share of a channel adds that share to the global counter in
+    // one GPU-scope atomic.  The pairs stored by the block's other warps are
+    // ordered before that atomic through the CTA-scope counter (release
+    // sequences compose), so the combine sees them all.
+    struct Counter {
+        unsigned *slots;          // shared counters, or nullptr: count each tile globally
+        unsigned bstart, bend, T, c_lo;   // 32-bit: block counting needs C*T < 2^31
+        // lane 0: counts the finished tile of channel c; true when that
+        // completes channel c
+        __device__ bool count(unsigned *cnt, int c) const
+        {
+            if (!slots) return atom_add_acq_rel_gpu(cnt + c, 1u) == T - 1u;
+            const unsigned lo = max(bstart, (unsigned)c * T), hi = min(bend, (unsigned)(c + 1) * T);
+            const unsigned mine = hi - lo;   // the block's tiles of c
+            if (atom_add_acq_rel_cta_shared(slots + (c - c_lo), 1u) + 1u != mine) return false;
+            return atom_add_acq_rel_gpu(cnt + c, mine) + mine == T;
+        }
+    };
+    // Block counting when the block's range [bstart, bend) spans at most
+    // kSlots channels (slots zeroed by the caller before the interval
+    // barrier) and every tile index fits in 31 bits.
+    static __device__ __forceinline__ Counter make_counter(unsigned *slots, unsigned long long bstart,
+                                                           unsigned long long bend, unsigned long long T,
+                                                           unsigned long long ntiles)
+    {
+        Counter k;
+        const bool fits = slots && ntiles < (1ull << 31) && bend > bstart &&
+                          (bend - 1) / T - bstart / T < (unsigned long long)kSlots;
+        k.slots = fits ? slots : nullptr;
+        k.bstart = (unsigned)bstart;
+        k.bend = (unsigned)bend;
+        k.T = (unsigned)T;
+        k.c_lo = fits ? (unsigned)(bstart / T) : 0u;
+        return k;
+    }
+
     // Tile assignment.  With the pool (a counter in the interval's shared
     // memory) block b owns a contiguous range of about C*T/grid tiles and
     // its warps take them in order one at a time, asking for the next one a
@@ -254,6 +301,8 @@ struct BodyBn {
         const unsigned long long q = ntiles / G, rem = ntiles % G;
         const unsigned long long bstart = b * q + (b < rem ? b : rem);
         const unsigned long long bend = bstart + q + (b < rem ? 1ull : 0ull);
+        const Counter counter = make_counter(pool ? pool + kPoolBytes / sizeof(unsigned) : nullptr, bstart, bend,
+                                             (unsigned long long)T, ntiles);
         unsigned long long tile;
         if (pool) {
             unsigned i = 0;
@@ -279,7 +328,7 @@ struct BodyBn {
             bool last = false;
             if (lane == 0) {
                 part[tile] = make_float2(s1, s2);
-                last = atom_add_acq_rel_gpu(cnt + c, 1u) == (unsigned)(T - 1);
+                last = counter.count(cnt, c);
             }
             last = __shfl_sync(0xffffffffu, last, 0);
             if (last) {
@@ -352,6 +401,7 @@ struct BodyBn {
             tl1 = grab();
             if (tl1 < ntiles) fill(1, tl1);
         }
+        const Counter counter = make_counter(pool + kPoolBytes / sizeof(unsigned), bstart, bend, T, ntiles);
         int s = 0;
         unsigned ph = 0;
         for (;;) {
@@ -392,7 +442,7 @@ struct BodyBn {
             bool last = false;
             if (lane == 0) {
                 part[tile] = make_float2(s1, s2);
-                last = atom_add_acq_rel_gpu(cnt + c, 1u) == (unsigned)(T - 1);
+                last = counter.count(cnt, c);
             }
             last = __shfl_sync(0xffffffffu, last, 0);
             if (last) {
@@ -410,9 +460,9 @@ struct BodyBn {
     {
         if (a.C <= 0) return;
         unsigned *pool = nullptr;
-        if (smem_fits(cx, kPoolBytes)) {
+        if (smem_fits(cx, kCountBytes)) {
             pool = reinterpret_cast<unsigned *>(cx.smem);
-            if (cx.tid == 0) *pool = 0u;
+            for (int i = cx.tid; i < (int)(kCountBytes / sizeof(unsigned)); i += cx.nthreads) pool[i] = 0u;
             interval_sync(cx);
         }
         if ((a.HW & 3) == 0 && aligned16(a.x)) {

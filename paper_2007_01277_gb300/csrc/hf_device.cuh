@@ -197,6 +197,16 @@ __device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned v
     return old;
 }
 
+// Atomic add on shared memory with acquire-release semantics at CTA scope;
+// returns the old value.
+__device__ __forceinline__ unsigned atom_add_acq_rel_cta_shared(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;"
+                 : "=r"(old) : "r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+    return old;
+}
+
 __host__ __device__ __forceinline__ bool aligned16(const void *p)
 {
     return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
