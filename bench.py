@@ -925,15 +925,18 @@ def cpu_sample_us(workload, cores):
 
 def cpu_baseline_for(workload: str, reps: int = 3):
     """The cpu_baseline object: the median of `reps` runs of the oracle on
-    the workload's sample, spread over every host core.  The reference arm
-    times the same sample per step."""
+    the workload's sample, spread over every host core, and one run of the
+    same jobs on a single thread.  The reference arm times the same sample
+    per step."""
     cores = os.cpu_count() or 1
     if cpu_jobs(workload, cores) is None:
         return None
-    _jobs, _scale, desc = cpu_jobs(workload, cores)
+    jobs, scale, desc = cpu_jobs(workload, cores)
     v = statistics.median(cpu_sample_us(workload, cores) for _ in range(reps))
+    one = _pool_time(jobs, 1) * scale * 1e6
     return {"value": round(v, 1), "unit": "us", "cores": cores, "kind": "oracle",
-            "sample": "%s; median of %d runs" % (desc, reps)}
+            "sample": "%s; median of %d runs" % (desc, reps),
+            "single_thread_us": round(one, 1)}
 
 
 def torch_int16():
