@@ -5,17 +5,21 @@
 // GB300 layout.  Channel c is the sequence of its M = N*HW values (N runs of
 // HW contiguous floats).  It is cut into tiles of TILE values; one warp
 // reduces one tile at a time (each block's warps share its contiguous range
-// of tiles through a counter in shared memory), streaming it with 128-bit
+// of tiles through a counter in shared memory).  A tile arrives either
+// through the warp's bulk-copy ring (its one to three runs copied into one
+// stage, the next tiles' copies in flight) or, without a ring, as 128-bit
 // loads, 16 per lane with 8 in flight.  Each tile yields FP32 sums of
 // d = x - K_c and d*d, where the shift K_c = x[0][c][0] keeps the variance
 // free of cancellation (the shifted-data algorithm, Chan, Golub & LeVeque
-// 1983).  A warp writes the tile's pair to the workspace and bumps a
-// per-channel counter (an acquire-release atomic); the warp that brings
-// channel c's counter to T combines that channel's T pairs in tile order
-// (double-float sums), writes mean/var and resets the counter.  The only
-// block-level barrier is the one after the pool counter is set; the
-// reduction order depends only on the tile size, so a fused interval and a
-// standalone launch give identical bits whatever their threads and grid.
+// 1983), in the same order on both paths.  A warp writes the tile's pair to
+// the workspace and counts the tile -- in the block's shared-memory counter
+// of channel c, the block's share then added to the global counter in one
+// acquire-release atomic; the warp that brings channel c's global counter to
+// T combines that channel's T pairs in tile order (double-float sums),
+// writes mean/var and resets the counter.  The only block-level barrier is
+// the one after the pool and the counters are set; the reduction order
+// depends only on the tile size, so a fused interval and a standalone launch
+// give identical bits whatever their threads, grid and path.
 #pragma once
 #include "hf_device.cuh"
 

@@ -225,10 +225,12 @@ namespace hf {
 // inside a fused block no longer depends on its share of the block's
 // warps.
 //
-// The geometry (stage bytes B, stages S) comes from the launch (Ctx): the
-// runtime sizes it for the whole SM -- all ring warps of all resident
-// blocks -- to about 40 KB in flight, where HBM bandwidth peaks; too much
-// in flight costs bandwidth.  Ring layout from `off` in the slice: nw x S
+// The geometry (stage bytes B, stages S) comes from the launch (Ctx).  For a
+// body that streams tiles of a flat array the runtime sizes it for the whole
+// SM -- all stream-ring warps of all resident blocks -- to about 40 KB in
+// flight, where a pure stream's bandwidth peaks; a body that takes one work
+// item per stage gets two stages of its item size.  Ring layout from `off`
+// in the slice: nw x S
 // stages of B bytes (warp w owns stages [w*S, w*S+S)), then nw x S 8-byte
 // barriers.  Every wait is bounded in time; when it expires the warp sets
 // kErrWaitExpired in the device error word, waits (bounded) for the copies
