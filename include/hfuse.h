@@ -525,8 +525,9 @@ void hf_src_unload(hf_src_module m);
  * Stream rings share about 40 KB in flight per SM over their warps, in
  * stages of 1, 2 or 4 KB, 2 to 4 per warp; intervals whose minimum the
  * share misses fall back to register loads.  Per interval: stage[i] bytes,
- * stages[i] (0 when no ring) and uses[i].  The launch drops item rings
- * first if they do not fit in shared memory.  Host arithmetic only. */
+ * stages[i] (0 when no ring) and uses[i].  When they do not fit in shared
+ * memory the launch drops item rings, the largest first, before it lowers
+ * the blocks per SM.  Host arithmetic only. */
 hf_status hf_ring_plan(int n, const int *warps, const int *ring, const unsigned *min_bytes,
                        int blocks_per_sm, unsigned *stage, int *stages, int *uses);
 

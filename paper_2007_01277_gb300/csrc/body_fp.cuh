@@ -15,8 +15,11 @@ namespace hf {
 // lane, advanced together by one packed FMA chain); warps take units in an
 // order that interleaves blocks (warp w of block b has rank w * grid + b),
 // so when the units do not divide evenly the extra ones land on every SM
-// alike instead of on the first blocks.  A warp runs two units at a time
-// (two independent chains per lane) while it has two left.
+// alike instead of on the first blocks.  A warp runs four units at a time
+// (four independent chains per lane) while it has four left, then two,
+// then one: in a fused block the polynomial has few warps per scheduler, and
+// independent chains are what covers the FMA latency while the other
+// bodies' warps take issue slots.
 struct BodyPoly {
     using Args = hf_poly_args;
     static constexpr int kId = HF_BODY_POLY;
@@ -79,6 +82,18 @@ struct BodyPoly {
         const int64_t nwt = (int64_t)cx.grid * (cx.nthreads >> 5);
         const int64_t lane2 = 2 * lane_id();
         int64_t u = (int64_t)(cx.tid >> 5) * cx.grid + cx.block;
+        for (; u + 3 * nwt < units; u += 4 * nwt) {
+            int64_t e[4];
+            unsigned long long x[4], r[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                e[j] = (u + j * nwt) * kUnit + lane2;
+                x[j] = load2(a, e[j]);
+            }
+            chains<4>(r, x, c, a.iters);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) store2(a, e[j], r[j]);
+        }
         for (; u + nwt < units; u += 2 * nwt) {
             const int64_t e0 = u * kUnit + lane2, e1 = (u + nwt) * kUnit + lane2;
             const unsigned long long x[2] = {load2(a, e0), load2(a, e1)};

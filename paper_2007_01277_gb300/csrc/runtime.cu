@@ -330,18 +330,18 @@ void ring_geom(double F, unsigned *stage, int *stages)
 }
 
 // The ring decision for `b` resident blocks of a block whose intervals have
-// warps[i] warps, ring kind kind[i] and ring_min[i].  Item rings (when
-// `items`) get their fixed geometry: stages of ring_min[i] bytes, two per
+// warps[i] warps, ring kind kind[i] and ring_min[i].  Item rings (where
+// item_ok[i], or everywhere when item_ok is NULL) get their fixed geometry: stages of ring_min[i] bytes, two per
 // warp.  Stream rings share about 40 KB in flight per SM over their warps
 // (the bf16 stream's optimum); intervals whose minimum the SM's share misses
 // drop their ring and the share is recomputed over the rest.  Returns which
 // intervals keep a ring and each one's stage bytes and stages.
 constexpr int kItemStages = 2;
-void ring_choice(int n, const int *warps, const int *kind, const unsigned *ring_min, int b, bool items,
-                 bool *use, unsigned *stage, int *stages)
+void ring_choice(int n, const int *warps, const int *kind, const unsigned *ring_min, int b,
+                 const bool *item_ok, bool *use, unsigned *stage, int *stages)
 {
     for (int i = 0; i < n; ++i) {
-        use[i] = b > 0 && (kind[i] == kRingStream || (kind[i] == kRingItem && items));
+        use[i] = b > 0 && (kind[i] == kRingStream || (kind[i] == kRingItem && (!item_ok || item_ok[i])));
         stage[i] = 0;
         stages[i] = 0;
     }
@@ -409,17 +409,27 @@ hf_status plan_launch(const void *func, int d0, int n, const int *threads, const
         return fail(HF_ERR_REGS, "block of %d threads with %zu B shared memory cannot be resident", d0,
                     base_total);
     if (want > 0) bmax = std::max(1, std::min(bmax, (want + lim.sm_count - 1) / lim.sm_count));
+    // item intervals, largest ring first: the order in which they give up
+    // their ring when shared memory runs out
+    int drop[HF_MAX_INTERVALS], n_item = 0;
+    for (int i = 0; i < n; ++i)
+        if (ring[i] == kRingItem) drop[n_item++] = i;
+    std::sort(drop, drop + n_item, [&](int x, int y) {
+        return (size_t)threads[x] * ring_min[x] > (size_t)threads[y] * ring_min[y];
+    });
     for (int b = bmax; b >= 0; --b)
-        for (int items = 1; items >= 0; --items) {
+        for (int k = 0; k <= n_item; ++k) {
             // b == 0: the last resort, no rings at the largest block count.
-            // Item rings that do not fit go before the block count drops;
-            // stream intervals whose body wants more in flight per warp than
-            // the SM's share gives drop their ring (register loads).
-            bool use[HF_MAX_INTERVALS];
+            // Item rings that do not fit go, largest first, before the block
+            // count drops; stream intervals whose body wants more in flight
+            // per warp than the SM's share gives drop their ring (register
+            // loads).
+            bool use[HF_MAX_INTERVALS], item_ok[HF_MAX_INTERVALS];
             int warps[HF_MAX_INTERVALS], stages[HF_MAX_INTERVALS];
             unsigned stage[HF_MAX_INTERVALS];
-            for (int i = 0; i < n; ++i) warps[i] = threads[i] / 32;
-            ring_choice(n, warps, ring, ring_min, b, items != 0, use, stage, stages);
+            for (int i = 0; i < n; ++i) warps[i] = threads[i] / 32, item_ok[i] = true;
+            for (int j = 0; j < k; ++j) item_ok[drop[j]] = false;
+            ring_choice(n, warps, ring, ring_min, b, item_ok, use, stage, stages);
             size_t off = 0;
             for (int i = 0; i < n; ++i) {
                 out->off[i] = (unsigned)off;
@@ -459,7 +469,7 @@ void interval_smem_at(const int *ids, const void *const *args, const int *thread
         mins[i] = valid_body(ids[i]) ? body_ops(ids[i]).ring_min : 0u;
         warps[i] = threads[i] / 32;
     }
-    ring_choice(2, warps, kind, mins, b, true, use, stage, stages);
+    ring_choice(2, warps, kind, mins, b, nullptr, use, stage, stages);
     for (int i = 0; i < 2; ++i) {
         const double base = valid_body(ids[i]) ? (double)body_ops(ids[i]).smem(threads[i], args[i]) : 0.0;
         out[i] = base + (use[i] && stages[i] > 0 ? (double)ring_bytes(threads[i], stage[i], stages[i]) : 0.0);
@@ -612,7 +622,7 @@ hf_status hf_ring_plan(int n, const int *warps, const int *ring, const unsigned 
         if (ring[i] < kRingNone || ring[i] > kRingItem) return fail(HF_ERR_INVALID, "bad ring kind");
         kind[i] = ring[i];
     }
-    ring_choice(n, warps, kind, min_bytes, blocks_per_sm, true, use, stage, stages);
+    ring_choice(n, warps, kind, min_bytes, blocks_per_sm, nullptr, use, stage, stages);
     for (int i = 0; i < n; ++i) uses[i] = use[i] ? 1 : 0;
     return HF_OK;
 }
