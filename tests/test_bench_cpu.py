@@ -51,3 +51,12 @@ def test_reference_arm_and_cpu_baseline_time_the_same_sample():
     # 64 channels and 2^20 elements in 4 slices each
     assert len(jobs) == 8
     assert bench.cpu_jobs("bn_poly", 4)[0] is jobs      # drawn once, cached
+
+
+def test_e2e_record_is_the_median_run():
+    link = {"h2d_gbs": 210.0, "d2h_gbs": 192.0, "h2d_alone_us": 5677.0, "d2h_alone_us": 7141.0,
+            "both_directions_us": 8016.0}
+    r = bench.e2e_record([8209.5, 13153.6, 8190.7], 1191706624, 1373113344, 20, link)
+    assert r["value"] == 8209.5 and r["runs_us"] == [8209.5, 13153.6, 8190.7]
+    assert r["h2d_bytes_per_step"] == 1191706624 and r["d2h_bytes_per_step"] == 1373113344
+    assert r["copy_bound_us"] == 8016.0 and "median of 3 runs of 20 steps" in r["mode"]

@@ -193,6 +193,21 @@ def test_philox(n, seed, first, threads, grid):
     assert np.array_equal(out.cpu().numpy().view(np.uint32), ref)
 
 
+@pytest.mark.parametrize("n", [1, 2, 7, 4097])
+def test_philox_output_alignments(n):
+    # output at byte offsets 0 and 16 (a 16-byte but not 32-byte aligned
+    # start): the same blocks, and nothing written outside the output
+    ref = oracle.philox4x32_10(5, n, first=3)
+    for off in (0, 1):
+        buf = torch.full((n + 2, 4), -1, dtype=torch.int32, device=DEV)
+        out = buf[off: off + n]
+        single(H.PHILOX, H.philox_args(out, 5, 3), 64, 3)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), ref)
+        rest = torch.cat([buf[:off], buf[off + n:]])
+        assert (rest == -1).all()
+
+
 @pytest.mark.parametrize("n,offset,iters", [(1, 0, 64), (5, 0, 64), (4099, 0, 64), (1000, 1, 64),
                                             (257, 0, 1), (64, 0, 0)])
 @pytest.mark.parametrize("threads,grid", [(256, 0), (64, 3)])
