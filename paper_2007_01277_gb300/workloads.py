@@ -42,24 +42,28 @@ BF16_ALPHA = 0.5
 SEED = 0
 
 
-def gen(seed: int) -> torch.Generator:
-    return torch.Generator().manual_seed(int(seed))
+def gen(seed: int, device=None) -> torch.Generator:
+    """The seeded generator: on the CPU by default.  Inputs of several GB
+    (the tests past 32-bit indexing) are drawn by the device's generator
+    instead, and the oracle gets the same bytes copied back."""
+    g = torch.Generator(device=device) if device is not None else torch.Generator()
+    return g.manual_seed(int(seed))
 
 
-def normal(shape, seed: int) -> torch.Tensor:
+def normal(shape, seed: int, device=None) -> torch.Tensor:
     """float32 ~N(0,1)."""
-    return torch.randn(*shape, generator=gen(seed), dtype=torch.float32)
+    return torch.randn(*shape, generator=gen(seed, device), dtype=torch.float32, device=device)
 
 
-def uniform(shape, lo: float, hi: float, seed: int) -> torch.Tensor:
+def uniform(shape, lo: float, hi: float, seed: int, device=None) -> torch.Tensor:
     """float32 ~U(lo, hi)."""
-    t = torch.rand(*shape, generator=gen(seed), dtype=torch.float32)
-    return t * (hi - lo) + lo
+    t = torch.rand(*shape, generator=gen(seed, device), dtype=torch.float32, device=device)
+    return t.mul_(hi - lo).add_(lo)
 
 
-def bytes_u8(n: int, seed: int) -> torch.Tensor:
+def bytes_u8(n: int, seed: int, device=None) -> torch.Tensor:
     """uint8 ~U[0, 255]."""
-    return torch.randint(0, 256, (n,), generator=gen(seed), dtype=torch.uint8)
+    return torch.randint(0, 256, (n,), generator=gen(seed, device), dtype=torch.uint8, device=device)
 
 
 def bf16_uniform(n: int, seed: int) -> torch.Tensor:
