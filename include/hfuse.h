@@ -453,14 +453,18 @@ typedef struct {
  * the twelve fastest is rebalanced up to six times from a traced launch
  * (hf_launch_traced), giving interval i warps in proportion to its warps
  * times its finishing time while that helps; from each of the five
- * fastest plans seen it then searches locally -- move one warp between two
- * intervals, move one kernel to another interval, swap two kernels of
- * different intervals, change the register cap -- taking the best neighbour
- * while the measured time drops by more than 0.5%; finally the five fastest
- * distinct plans are timed again with 3 * reps launches and the fastest of
- * those is returned.  The seeds (at most 30) and the final timings are
- * always done; max_evals bounds the total including the seeds for the
- * phases between.
+ * fastest plans seen it then searches locally -- move one or two warps
+ * between two intervals, move one kernel to another interval, swap two
+ * kernels of different intervals, change the register cap -- taking the
+ * best neighbour while the measured time drops by more than 0.5%; the
+ * budget left after that goes to restarts (at most 64): two or three random
+ * moves away from the fastest plan so far (every other restart one of them
+ * moves three or four warps; a fixed-seed generator, so the search depends
+ * only on the measured times), then the same local search.  Finally the
+ * five fastest distinct plans are timed again with 3 * reps launches and
+ * the fastest of those is returned.  The seeds (at most 30) and the final
+ * timings are always done; max_evals bounds the total including the seeds
+ * for the phases between.
  * standalone_us (n entries, may be NULL) receives the single-kernel times. */
 hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, int max_evals,
                            int reps, int flush_l2, void *stream, hf_nway_plan *best,

@@ -428,53 +428,57 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
         if (!dup) starts.push_back(sd.p);
         if (starts.size() == 5) break;
     }
-    for (const NwayPlanC &start : starts) {
-        NwayPlanC cur = start;
-        float cur_t = -1.f;
-        for (const Seed &sd : seen)
-            if (same(sd.p, start)) {
-                cur_t = sd.t;
-                break;
+    // the neighbours of a plan: one or two warps moved between two
+    // intervals, one kernel moved to another interval, two kernels of
+    // different intervals swapped, or the same plan under another register
+    // cap
+    auto neighbours = [&](const NwayPlanC &base) {
+        std::vector<NwayPlanC> nb;
+        for (int w = 1; w <= 2; ++w)
+            for (int i = 0; i < base.P; ++i)
+                for (int j = 0; j < base.P; ++j) {
+                    if (i == j || base.warps[i] <= w) continue;
+                    NwayPlanC p = base;
+                    p.warps[i] -= w;
+                    p.warps[j] += w;
+                    nb.push_back(p);
+                }
+        for (int k = 0; k < n; ++k)
+            for (int j = 0; j < base.P; ++j) {
+                if (j == base.io[k]) continue;
+                NwayPlanC p = base;
+                p.io[k] = j;
+                if (used_all(p)) nb.push_back(p);
             }
+        for (int k = 0; k < n; ++k)
+            for (int l = k + 1; l < n; ++l) {
+                if (base.io[k] == base.io[l]) continue;
+                NwayPlanC p = base;
+                std::swap(p.io[k], p.io[l]);
+                nb.push_back(p);
+            }
+        for (int cap : caps) {
+            if (cap == base.cap) continue;
+            NwayPlanC p = base;
+            p.cap = cap;
+            nb.push_back(p);
+        }
+        return nb;
+    };
+    // steepest descent from `start` (measured at start_t, < 0 if not yet):
+    // take the best neighbour while it is faster by more than 0.5 %
+    auto local_search = [&](const NwayPlanC &start, float start_t) -> hf_status {
+        NwayPlanC cur = start;
+        float cur_t = start_t;
         bool improved = true;
         while (improved && evals < max_evals) {
             improved = false;
-            const NwayPlanC base = cur;
-            std::vector<NwayPlanC> nb;
-            for (int i = 0; i < base.P; ++i)
-                for (int j = 0; j < base.P; ++j) {
-                    if (i == j || base.warps[i] <= 1) continue;
-                    NwayPlanC p = base;
-                    --p.warps[i];
-                    ++p.warps[j];
-                    nb.push_back(p);
-                }
-            for (int k = 0; k < n; ++k)
-                for (int j = 0; j < base.P; ++j) {
-                    if (j == base.io[k]) continue;
-                    NwayPlanC p = base;
-                    p.io[k] = j;
-                    if (used_all(p)) nb.push_back(p);
-                }
-            for (int k = 0; k < n; ++k)
-                for (int l = k + 1; l < n; ++l) {
-                    if (base.io[k] == base.io[l]) continue;
-                    NwayPlanC p = base;
-                    std::swap(p.io[k], p.io[l]);
-                    nb.push_back(p);
-                }
-            for (int cap : caps) {   // same plan under another register cap
-                if (cap == base.cap) continue;
-                NwayPlanC p = base;
-                p.cap = cap;
-                nb.push_back(p);
-            }
             float step_t = cur_t;
             NwayPlanC step_p = cur;
-            for (const NwayPlanC &p : nb) {
+            for (const NwayPlanC &p : neighbours(cur)) {
                 if (evals >= max_evals) break;
-                st = consider(p);
-                if (st) return st;
+                const hf_status s2 = consider(p);
+                if (s2) return s2;
                 if (last_t > 0.f && (step_t < 0.f || last_t < step_t)) {
                     step_t = last_t;
                     step_p = p;
@@ -486,8 +490,53 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
                 improved = true;
             }
         }
+        return HF_OK;
+    };
+    for (const NwayPlanC &start : starts) {
+        float t0 = -1.f;
+        for (const Seed &sd : seen)
+            if (same(sd.p, start)) {
+                t0 = sd.t;
+                break;
+            }
+        st = local_search(start, t0);
+        if (st) return st;
     }
-    // 5. the fastest few distinct plans again with three times the
+    // 5. iterated local search with what is left of the budget: two or
+    //    three random moves away from the fastest plan so far (one of them,
+    //    every other restart, three or four warps moved between two
+    //    intervals), then steepest descent again.  The generator has a fixed
+    //    seed (SplitMix64), so the search depends only on the measured times.
+    unsigned long long rs = 0x2007012770000001ull;
+    auto rnd = [&](size_t m) {
+        rs += 0x9E3779B97F4A7C15ull;
+        unsigned long long z = rs;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return (size_t)((z ^ (z >> 31)) % m);
+    };
+    for (int restart = 0; restart < 64 && evals + 8 < max_evals; ++restart) {
+        NwayPlanC p = bp;
+        if (restart % 2 == 1 && p.P > 1) {
+            const int w = 3 + (int)rnd(2), i = (int)rnd(p.P), j = (i + 1 + (int)rnd(p.P - 1)) % p.P;
+            if (p.warps[i] > w) {
+                p.warps[i] -= w;
+                p.warps[j] += w;
+            }
+        }
+        const int moves = 2 + (int)rnd(2) - (restart % 2);
+        for (int m = 0; m < moves; ++m) {
+            const std::vector<NwayPlanC> nb = neighbours(p);
+            if (nb.empty()) break;
+            p = nb[rnd(nb.size())];
+        }
+        st = consider(p);
+        if (st) return st;
+        if (last_t <= 0.f) continue;
+        st = local_search(p, last_t);
+        if (st) return st;
+    }
+    // 6. the fastest few distinct plans again with three times the
     //    repetitions: a single noisy timing should not pick the winner
     std::sort(seen.begin(), seen.end(), [](const Seed &a, const Seed &b) { return a.t < b.t; });
     std::vector<Seed> finalists;

@@ -398,6 +398,36 @@ def test_nway_shared_interval_schedule():
             assert torch.equal(u, v)
 
 
+def test_nway_kernel_cut_across_intervals():
+    """One kernel's range cut into two kernels of the same body on different
+    intervals (bf16 by elements, Philox by counter offset, upsample by
+    planes) gives the bits of one standalone launch over the whole range."""
+    n16 = 8 * 5003
+    x16, y16 = (t.to(DEV) for t in W.bf16_inputs(n16, 31))
+    xu = W.upsample_input((6, 1, 20, 24), 32).to(DEV)
+    np_, m16, mp, mu = 10007, 8 * 2001, 4096, 2
+    o16, po, yu = (torch.empty_like(x16), torch.empty((np_, 4), dtype=torch.int32, device=DEV),
+                   torch.empty((6, 1, 40, 48), device=DEV))
+    parts = [(H.BF16_AXPY, H.bf16_axpy_args(x16[:m16], y16[:m16], o16[:m16]), 0),
+             (H.PHILOX, H.philox_args(po[:mp], 7, 5), 0),
+             (H.UPSAMPLE2X, H.upsample2x_args(xu[:mu], yu[:mu]), 1),
+             (H.BF16_AXPY, H.bf16_axpy_args(x16[m16:], y16[m16:], o16[m16:]), 1),
+             (H.PHILOX, H.philox_args(po[mp:], 7, 5 + mp), 2),
+             (H.UPSAMPLE2X, H.upsample2x_args(xu[mu:], yu[mu:]), 2)]
+    ks = [H.hf_register_kernel(b) for b, _, _ in parts]
+    f = H.hf_fuse_n(ks, [i for _, _, i in parts], [96, 128, 64], 0)
+    H.hf_launch(f, [a for _, a, _ in parts], grid=11)
+    r16, rpo, ryu = torch.empty_like(o16), torch.empty_like(po), torch.empty_like(yu)
+    single(H.BF16_AXPY, H.bf16_axpy_args(x16, y16, r16), 128, 11)
+    single(H.PHILOX, H.philox_args(rpo, 7, 5), 128, 11)
+    single(H.UPSAMPLE2X, H.upsample2x_args(xu, ryu), 128, 11)
+    torch.cuda.synchronize()
+    assert H.hf_check_device_error() == 0
+    assert torch.equal(o16, r16) and torch.equal(po, rpo) and torch.equal(yu, ryu)
+    assert np.array_equal(rpo.cpu().numpy().view(np.uint32), oracle.philox4x32_10(7, np_, first=5))
+    H.hf_destroy_fused(f)
+
+
 def test_stream_wait_and_query():
     k = H.hf_register_kernel(H.POLY)
     x = torch.rand(1 << 16, device=DEV)
