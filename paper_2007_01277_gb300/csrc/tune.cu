@@ -465,9 +465,22 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
         }
         return nb;
     };
-    // steepest descent from `start` (measured at start_t, < 0 if not yet):
-    // take the best neighbour while it is faster by more than 0.5 %
-    auto local_search = [&](const NwayPlanC &start, float start_t) -> hf_status {
+    // Random numbers of the restarts below: SplitMix64 from a fixed seed, so
+    // the search depends only on the measured times.
+    unsigned long long rs = 0x2007012770000001ull;
+    auto rnd = [&](size_t m) {
+        rs += 0x9E3779B97F4A7C15ull;
+        unsigned long long z = rs;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return (size_t)((z ^ (z >> 31)) % m);
+    };
+    // Local search from `start` (measured at start_t, < 0 if not yet).
+    // Steepest descent: take the best neighbour while it is faster by more
+    // than 0.5 %.  First improvement (the restarts): visit the neighbours in
+    // random order and move to the first one faster by more than 0.5 %, so
+    // that a restart costs a few dozen evaluations rather than a few hundred.
+    auto local_search = [&](const NwayPlanC &start, float start_t, bool first) -> hf_status {
         NwayPlanC cur = start;
         float cur_t = start_t;
         bool improved = true;
@@ -475,13 +488,17 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
             improved = false;
             float step_t = cur_t;
             NwayPlanC step_p = cur;
-            for (const NwayPlanC &p : neighbours(cur)) {
+            std::vector<NwayPlanC> nb = neighbours(cur);
+            if (first)
+                for (size_t i = nb.size(); i > 1; --i) std::swap(nb[i - 1], nb[rnd(i)]);
+            for (const NwayPlanC &p : nb) {
                 if (evals >= max_evals) break;
                 const hf_status s2 = consider(p);
                 if (s2) return s2;
                 if (last_t > 0.f && (step_t < 0.f || last_t < step_t)) {
                     step_t = last_t;
                     step_p = p;
+                    if (first && cur_t > 0.f && step_t < cur_t * 0.995f) break;
                 }
             }
             if (step_t > 0.f && (cur_t < 0.f || step_t < cur_t * 0.995f)) {
@@ -499,32 +516,43 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
                 t0 = sd.t;
                 break;
             }
-        st = local_search(start, t0);
+        st = local_search(start, t0, false);
         if (st) return st;
     }
-    // 5. iterated local search with what is left of the budget: two or
-    //    three random moves away from the fastest plan so far (one of them,
-    //    every other restart, three or four warps moved between two
-    //    intervals), then steepest descent again.  The generator has a fixed
-    //    seed (SplitMix64), so the search depends only on the measured times.
-    unsigned long long rs = 0x2007012770000001ull;
-    auto rnd = [&](size_t m) {
-        rs += 0x9E3779B97F4A7C15ull;
-        unsigned long long z = rs;
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-        return (size_t)((z ^ (z >> 31)) % m);
+    // 5. iterated local search with what is left of the budget: a few
+    //    random moves away from one of the three fastest plans so far (every
+    //    other restart one of them moves three or four warps between two
+    //    intervals), or -- every third restart -- three or four warps moved
+    //    in one of the packing seeds of phase 2, then first-improvement local
+    //    search.
+    // the three fastest distinct plans measured so far
+    auto elites = [&] {
+        std::vector<Seed> v = seen;
+        std::sort(v.begin(), v.end(), [](const Seed &a, const Seed &b) { return a.t < b.t; });
+        std::vector<NwayPlanC> e;
+        for (const Seed &sd : v) {
+            bool dup = false;
+            for (const NwayPlanC &q : e) dup = dup || same(q, sd.p);
+            if (!dup) e.push_back(sd.p);
+            if (e.size() == 3) break;
+        }
+        return e;
     };
-    for (int restart = 0; restart < 64 && evals + 8 < max_evals; ++restart) {
-        NwayPlanC p = bp;
-        if (restart % 2 == 1 && p.P > 1) {
+    for (int restart = 0; restart < 512 && evals + 8 < max_evals; ++restart) {
+        // start from one of the three fastest plans in turn (one lucky timing
+        // of a mediocre plan should not hold every restart), or from a
+        // packing seed, whose structure may lie far from the plans so far
+        const std::vector<NwayPlanC> el = elites();
+        const bool from_seed = restart % 3 == 2 && !seeds.empty();
+        NwayPlanC p = from_seed ? seeds[rnd(seeds.size())].p : el.empty() ? bp : el[(size_t)restart % el.size()];
+        if ((from_seed || restart % 2 == 1) && p.P > 1) {
             const int w = 3 + (int)rnd(2), i = (int)rnd(p.P), j = (i + 1 + (int)rnd(p.P - 1)) % p.P;
             if (p.warps[i] > w) {
                 p.warps[i] -= w;
                 p.warps[j] += w;
             }
         }
-        const int moves = 2 + (int)rnd(2) - (restart % 2);
+        const int moves = from_seed ? 0 : 2 + (int)rnd(2) - (restart % 2);
         for (int m = 0; m < moves; ++m) {
             const std::vector<NwayPlanC> nb = neighbours(p);
             if (nb.empty()) break;
@@ -533,10 +561,10 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
         st = consider(p);
         if (st) return st;
         if (last_t <= 0.f) continue;
-        st = local_search(p, last_t);
+        st = local_search(p, last_t, true);
         if (st) return st;
     }
-    // 6. the fastest few distinct plans again with three times the
+    // 6. the ten fastest distinct plans again with three times the
     //    repetitions: a single noisy timing should not pick the winner
     std::sort(seen.begin(), seen.end(), [](const Seed &a, const Seed &b) { return a.t < b.t; });
     std::vector<Seed> finalists;
@@ -544,7 +572,7 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
         bool dup = false;
         for (const Seed &q : finalists) dup = dup || same(q.p, sd.p);
         if (!dup) finalists.push_back(sd);
-        if (finalists.size() == 5) break;
+        if (finalists.size() == 10) break;
     }
     if (finalists.size() > 1) {
         float best_conf = -1.f;
