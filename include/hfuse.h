@@ -472,6 +472,21 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
                            int reps, int flush_l2, void *stream, hf_nway_plan *best,
                            float *standalone_us);
 
+/* A plan's cost for hf_nway_search_sim: the time of `plan` (> 0; 0 or less
+ * when the plan cannot run), and each interval's finishing time (relative
+ * to the earliest start, any unit) in interval_finish[0 .. n_intervals). */
+typedef float (*hf_plan_cost_fn)(const hf_nway_plan *plan, float *interval_finish, void *user);
+
+/* The search of hf_autotune_nway (phases after the standalone timings) run
+ * against a cost function instead of the GPU, so that the search itself can
+ * be tested on the host: standalone_us[0..n) stand in for the kernels'
+ * standalone times, `cost` is asked wherever hf_autotune_nway would time a
+ * plan, trace a launch or time a finalist again.  best->evals counts the
+ * plans asked for; best->grid is 0.  The library keeps nothing of `user`.
+ * Returns HF_ERR_INVALID for bad arguments or when no plan has a cost. */
+hf_status hf_nway_search_sim(int n, const float *standalone_us, hf_plan_cost_fn cost, void *user,
+                             int max_evals, hf_nway_plan *best);
+
 /* ------------------------------------------------------------------ */
 /* Source-level front-end: Algorithm 1 (Sec. 3.1) as a transformation of
  * CUDA source text (the paper's automatic tool, Sec. 3.3), compiled at run

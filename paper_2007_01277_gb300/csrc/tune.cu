@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <vector>
 
@@ -228,40 +229,38 @@ hf_status hf_search_alg2(hf_kernel a, hf_kernel b, const void *const *args, int 
 }
 
 
-hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, int max_evals,
-                           int reps, int flush_l2_, void *stream, hf_nway_plan *best,
-                           float *standalone_us)
+} // extern "C"
+
+namespace {
+
+// The measurements the N-way search asks for.  The same search runs on the
+// GPU (hf_autotune_nway: each plan built, queried and timed) and against a
+// cost function the caller gives (hf_nway_search_sim: the search itself
+// tested on the host).
+struct NwayMeasure {
+    // time plan p: HF_OK with *us > 0 and the grid used, another status when
+    // the plan cannot be built or is not resident (skipped); HF_ERR_CUDA ends
+    // the search
+    std::function<hf_status(const NwayPlanC &, float *, int *)> time;
+    // each interval's finishing time of plan p launched on `grid` blocks,
+    // relative to the earliest start (any unit)
+    std::function<hf_status(const NwayPlanC &, int, double *)> finish;
+    // time plan p again with three times the repetitions
+    std::function<hf_status(const NwayPlanC &, int, float *)> retime;
+};
+
+// The search of hf_autotune_nway over plans for n kernels whose standalone
+// times (phase 1, measured by the caller) are t[0..n): phases 2-6 below.
+hf_status nway_search(int n, const float *t, int max_evals, const NwayMeasure &m, hf_nway_plan *best)
 {
-    if (!ks || !args || !best || n < 1 || n > HF_MAX_SCHEDULE || reps < 1) return HF_ERR_INVALID;
-    hf_device_limits lim;
-    hf_status st = hf_device_info(&lim);
-    if (st) return st;
-    // 1. each kernel alone (256 threads, resident grid): its load
-    std::vector<float> t(n);
-    for (int k = 0; k < n; ++k) {
-        st = hf_time_single(ks[k], args[k], 256, 0, reps, flush_l2_, stream, &t[k], nullptr, nullptr);
-        if (st) return st;
-        if (standalone_us) standalone_us[k] = t[k];
-    }
+    hf_status st = HF_OK;
     int evals = 0;
     float best_t = -1.f;
     NwayPlanC bp;
     std::memset(&bp, 0, sizeof bp);
     auto eval = [&](const NwayPlanC &p, float *us, int *grid) -> hf_status {
-        int thr[HF_MAX_INTERVALS];
-        for (int i = 0; i < p.P; ++i) thr[i] = 32 * p.warps[i];
-        hf_fused f = nullptr;
-        hf_status s2 = hf_fuse_n(ks, n, p.io, thr, p.P, p.cap, &f);
-        if (s2) return s2;
-        hf_fused_info info;
-        s2 = hf_query(f, args, &info);
-        if (!s2) {
-            *grid = info.blocks_per_sm * lim.sm_count;
-            s2 = hf_time_fused(f, args, *grid, reps, flush_l2_, stream, us, nullptr, nullptr);
-        }
-        hf_destroy_fused(f);
         ++evals;
-        return s2;
+        return m.time(p, us, grid);
     };
     struct Seed {
         float t;
@@ -333,37 +332,20 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
     // 3. rebalance from measured interval finishing times: interval i gets
     //    warps in proportion to warps_i * finish_i, so that intervals that
     //    end early give warps to the ones that end late
-    unsigned long long *d_trace = nullptr;
-    if (cudaMalloc(&d_trace, 2 * HF_MAX_INTERVALS * sizeof(unsigned long long)) != cudaSuccess)
-        return HF_ERR_CUDA;
     for (const Seed &sd : seeds) {
     NwayPlanC cur = sd.p;
     int cur_grid = sd.grid;
     float cur_t = sd.t;
     for (int round = 0; round < 6 && evals < max_evals; ++round) {
         const NwayPlanC base = cur;
-        int thr[HF_MAX_INTERVALS];
-        for (int i = 0; i < base.P; ++i) thr[i] = 32 * base.warps[i];
-        hf_fused f = nullptr;
-        if (hf_fuse_n(ks, n, base.io, thr, base.P, base.cap, &f)) break;
-        unsigned long long h[2 * HF_MAX_INTERVALS];
-        for (int i = 0; i < base.P; ++i) h[2 * i] = ~0ull, h[2 * i + 1] = 0ull;
-        cudaStream_t cs = static_cast<cudaStream_t>(stream);
-        bool ok = cudaMemcpyAsync(d_trace, h, sizeof h, cudaMemcpyHostToDevice, cs) == cudaSuccess &&
-                  hf_launch_traced(f, args, cur_grid, stream, d_trace) == HF_OK &&
-                  cudaMemcpyAsync(h, d_trace, sizeof h, cudaMemcpyDeviceToHost, cs) == cudaSuccess &&
-                  cudaStreamSynchronize(cs) == cudaSuccess;
-        hf_destroy_fused(f);
-        if (!ok) {
-            cudaFree(d_trace);
-            return HF_ERR_CUDA;
-        }
-        unsigned long long t0 = ~0ull;
-        for (int i = 0; i < base.P; ++i) t0 = std::min(t0, h[2 * i]);
+        double fin[HF_MAX_INTERVALS];
+        const hf_status s2 = m.finish(base, cur_grid, fin);
+        if (s2 == HF_ERR_CUDA) return s2;
+        if (s2) break;
         const int W = [&] { int w = 0; for (int i = 0; i < base.P; ++i) w += base.warps[i]; return w; }();
         double want[HF_MAX_INTERVALS], tot = 0.0;
         for (int i = 0; i < base.P; ++i) {
-            want[i] = base.warps[i] * (double)(h[2 * i + 1] - t0);
+            want[i] = base.warps[i] * fin[i];
             tot += want[i];
         }
         if (tot <= 0.0) break;
@@ -390,17 +372,13 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
         }
         if (std::equal(p.warps, p.warps + p.P, base.warps)) break;
         st = consider(p);
-        if (st) {
-            cudaFree(d_trace);
-            return st;
-        }
+        if (st) return st;
         if (!(last_t > 0.f && last_t < cur_t)) break;   // this seed stopped improving
         cur = p;
         cur_t = last_t;
         cur_grid = last_grid;
     }
     }
-    cudaFree(d_trace);
     // 4. local search from the fastest plan: move one warp between two
     //    intervals, move one kernel to another interval, or swap two kernels
     //    of different intervals; take the best neighbour while it helps
@@ -577,13 +555,8 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
     if (finalists.size() > 1) {
         float best_conf = -1.f;
         for (const Seed &sd : finalists) {
-            int thr[HF_MAX_INTERVALS];
-            for (int i = 0; i < sd.p.P; ++i) thr[i] = 32 * sd.p.warps[i];
-            hf_fused f = nullptr;
-            if (hf_fuse_n(ks, n, sd.p.io, thr, sd.p.P, sd.p.cap, &f)) continue;
             float us = 0.f;
-            const hf_status s2 = hf_time_fused(f, args, sd.grid, 3 * reps, flush_l2_, stream, &us, nullptr, nullptr);
-            hf_destroy_fused(f);
+            const hf_status s2 = m.retime(sd.p, sd.grid, &us);
             ++evals;
             if (s2 == HF_ERR_CUDA) return s2;
             if (s2) continue;
@@ -605,6 +578,113 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
     best->time_us = best_t;
     best->evals = evals;
     return HF_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, int max_evals,
+                           int reps, int flush_l2_, void *stream, hf_nway_plan *best,
+                           float *standalone_us)
+{
+    if (!ks || !args || !best || n < 1 || n > HF_MAX_SCHEDULE || reps < 1) return HF_ERR_INVALID;
+    hf_device_limits lim;
+    hf_status st = hf_device_info(&lim);
+    if (st) return st;
+    // each kernel alone (256 threads, resident grid): its load
+    std::vector<float> t(n);
+    for (int k = 0; k < n; ++k) {
+        st = hf_time_single(ks[k], args[k], 256, 0, reps, flush_l2_, stream, &t[k], nullptr, nullptr);
+        if (st) return st;
+        if (standalone_us) standalone_us[k] = t[k];
+    }
+    unsigned long long *d_trace = nullptr;
+    if (cudaMalloc(&d_trace, 2 * HF_MAX_INTERVALS * sizeof(unsigned long long)) != cudaSuccess)
+        return HF_ERR_CUDA;
+    auto build = [&](const NwayPlanC &p, hf_fused *f) {
+        int thr[HF_MAX_INTERVALS];
+        for (int i = 0; i < p.P; ++i) thr[i] = 32 * p.warps[i];
+        return hf_fuse_n(ks, n, p.io, thr, p.P, p.cap, f);
+    };
+    NwayMeasure m;
+    m.time = [&](const NwayPlanC &p, float *us, int *grid) -> hf_status {
+        hf_fused f = nullptr;
+        hf_status s2 = build(p, &f);
+        if (s2) return s2;
+        hf_fused_info info;
+        s2 = hf_query(f, args, &info);
+        if (!s2) {
+            *grid = info.blocks_per_sm * lim.sm_count;
+            s2 = hf_time_fused(f, args, *grid, reps, flush_l2_, stream, us, nullptr, nullptr);
+        }
+        hf_destroy_fused(f);
+        return s2;
+    };
+    m.finish = [&](const NwayPlanC &p, int grid, double *fin) -> hf_status {
+        hf_fused f = nullptr;
+        if (build(p, &f)) return HF_ERR_INVALID;
+        unsigned long long h[2 * HF_MAX_INTERVALS];
+        for (int i = 0; i < p.P; ++i) h[2 * i] = ~0ull, h[2 * i + 1] = 0ull;
+        cudaStream_t cs = static_cast<cudaStream_t>(stream);
+        const bool ok = cudaMemcpyAsync(d_trace, h, sizeof h, cudaMemcpyHostToDevice, cs) == cudaSuccess &&
+                        hf_launch_traced(f, args, grid, stream, d_trace) == HF_OK &&
+                        cudaMemcpyAsync(h, d_trace, sizeof h, cudaMemcpyDeviceToHost, cs) == cudaSuccess &&
+                        cudaStreamSynchronize(cs) == cudaSuccess;
+        hf_destroy_fused(f);
+        if (!ok) return HF_ERR_CUDA;
+        unsigned long long t0 = ~0ull;
+        for (int i = 0; i < p.P; ++i) t0 = std::min(t0, h[2 * i]);
+        for (int i = 0; i < p.P; ++i) fin[i] = (double)(h[2 * i + 1] - t0);
+        return HF_OK;
+    };
+    m.retime = [&](const NwayPlanC &p, int grid, float *us) -> hf_status {
+        hf_fused f = nullptr;
+        if (build(p, &f)) return HF_ERR_INVALID;
+        const hf_status s2 = hf_time_fused(f, args, grid, 3 * reps, flush_l2_, stream, us, nullptr, nullptr);
+        hf_destroy_fused(f);
+        return s2;
+    };
+    st = nway_search(n, t.data(), max_evals, m, best);
+    cudaFree(d_trace);
+    return st;
+}
+
+hf_status hf_nway_search_sim(int n, const float *standalone_us, hf_plan_cost_fn cost, void *user,
+                             int max_evals, hf_nway_plan *best)
+{
+    if (!standalone_us || !cost || !best || n < 1 || n > HF_MAX_SCHEDULE) return HF_ERR_INVALID;
+    for (int k = 0; k < n; ++k)
+        if (!(standalone_us[k] > 0.f)) return HF_ERR_INVALID;
+    auto ask = [&](const NwayPlanC &p, float *fin) -> float {
+        hf_nway_plan q;
+        std::memset(&q, 0, sizeof q);
+        q.n_intervals = p.P;
+        for (int k = 0; k < n; ++k) q.interval_of[k] = p.io[k];
+        for (int i = 0; i < p.P; ++i) q.interval_threads[i] = 32 * p.warps[i];
+        q.regcap = p.cap;
+        return cost(&q, fin, user);
+    };
+    NwayMeasure m;
+    m.time = [&](const NwayPlanC &p, float *us, int *grid) -> hf_status {
+        float fin[HF_MAX_INTERVALS] = {0.f};
+        const float v = ask(p, fin);
+        if (!(v > 0.f)) return HF_ERR_INVALID;
+        *us = v;
+        *grid = 0;
+        return HF_OK;
+    };
+    m.finish = [&](const NwayPlanC &p, int, double *fin) -> hf_status {
+        float f[HF_MAX_INTERVALS] = {0.f};
+        if (!(ask(p, f) > 0.f)) return HF_ERR_INVALID;
+        for (int i = 0; i < p.P; ++i) fin[i] = f[i];
+        return HF_OK;
+    };
+    m.retime = [&](const NwayPlanC &p, int, float *us) -> hf_status {
+        int grid = 0;
+        return m.time(p, us, &grid);
+    };
+    return nway_search(n, standalone_us, max_evals, m, best);
 }
 
 } // extern "C"

@@ -120,6 +120,10 @@ class NwayPlan(ctypes.Structure):
                 "grid": self.grid, "time_us": self.time_us, "evals": self.evals}
 
 
+# cost function of hf_nway_search_sim: (plan, interval finishing times out, user) -> time
+PlanCostFn = ctypes.CFUNCTYPE(_f32, ctypes.POINTER(NwayPlan), ctypes.POINTER(_f32), _P)
+
+
 class BodyWork(ctypes.Structure):
     _fields_ = [("bytes", ctypes.c_double), ("ffma", ctypes.c_double), ("imul", ctypes.c_double),
                 ("smem_atomic", ctypes.c_double), ("ialu", ctypes.c_double), ("barriers", _i32),
@@ -178,6 +182,8 @@ def _load():
         "hf_bn_stats_noalloc": (_i32, [_P, _P, _P, _i32, _i32, _i32, _i32, _i32, _P]),
         "hf_autotune_nway": (_i32, [ctypes.POINTER(_P), _i32, ctypes.POINTER(_P), _i32, _i32, _i32,
                                     _P, ctypes.POINTER(NwayPlan), ctypes.POINTER(_f32)]),
+        "hf_nway_search_sim": (_i32, [_i32, ctypes.POINTER(_f32), PlanCostFn, _P, _i32,
+                                      ctypes.POINTER(NwayPlan)]),
         "hf_calibrate": (_i32, [_i32, _P, ctypes.POINTER(ctypes.c_double)]),
         "hf_src_fuse": (_i32, [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, _i32,
                                _i32, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
@@ -479,6 +485,28 @@ def hf_autotune_nway(kernels, args, max_evals=200, reps=5, flush_l2=False, strea
     d = plan.as_dict()
     d["interval_of"] = d["interval_of"][:n]
     return d, list(single)
+
+
+def hf_nway_search_sim(standalone_us, cost, max_evals=200):
+    """The N-way search against cost(plan_dict) -> (time, [finish per
+    interval]) instead of the GPU; returns the plan dict (with "evals")."""
+    n = len(standalone_us)
+
+    def cb(plan_p, fin_p, _user):
+        q = plan_p.contents.as_dict()
+        q["interval_of"] = q["interval_of"][:n]
+        t, fin = cost(q)
+        for i, v in enumerate(fin[:q["n_intervals"]]):
+            fin_p[i] = v
+        return t
+
+    fn = PlanCostFn(cb)
+    plan = NwayPlan()
+    _check("hf_nway_search_sim", lib.hf_nway_search_sim(n, (_f32 * n)(*standalone_us), fn, None,
+                                                        max_evals, ctypes.byref(plan)))
+    d = plan.as_dict()
+    d["interval_of"] = d["interval_of"][:n]
+    return d
 
 
 CAL_FFMA, CAL_IMUL, CAL_SMEM_ATOMIC, CAL_IALU = 0, 1, 2, 3
