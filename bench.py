@@ -998,7 +998,7 @@ def main():
                     choices=sorted(PAIR_SPECS) + ["nway8", "cost_model", "table2", "ratio_sweep"])
     ap.add_argument("--cost-db", default=None)
     ap.add_argument("--cost-steps", type=int, default=20000)
-    ap.add_argument("--nway-evals", type=int, default=5000)
+    ap.add_argument("--nway-evals", type=int, default=10000)
     ap.add_argument("--no-pairs", action="store_true",
                     help="8-way workload only: skip the fused-pair records")
     ap.add_argument("--no-cost-model", action="store_true",

@@ -457,13 +457,14 @@ typedef struct {
  * between two intervals, move one kernel to another interval, swap two
  * kernels of different intervals, change the register cap -- taking the
  * best neighbour while the measured time drops by more than 0.5%; the
- * budget left after that goes to restarts (at most 512): a few random
- * moves away from one of the three fastest plans so far, in turn (every
- * other restart one of the moves shifts three or four warps), or every
- * third restart three or four warps shifted in one of the packing seeds,
- * each followed by a first-improvement local search over the same moves in
- * random order (a fixed-seed generator, so the search depends only on the
- * measured times).  Finally the ten fastest distinct plans are timed
+ * budget left after that goes to restarts (at most 512), each from a few
+ * random moves (or three or four warps shifted) away from, in turn, one of
+ * the three fastest plans so far, the fastest plan of one block size and
+ * register cap (the families in turn, so that one that started behind is
+ * still refined), or one of the packing seeds, and each followed by a
+ * first-improvement local search over the same moves in random order (a
+ * fixed-seed generator, so the search depends only on the measured
+ * times).  Finally the ten fastest distinct plans are timed
  * again with 3 * reps launches and the fastest of those is returned.  The
  * seeds (at most 30) and the final timings are always done; max_evals
  * bounds the total including the seeds for the phases between.

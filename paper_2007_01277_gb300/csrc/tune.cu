@@ -497,18 +497,24 @@ hf_status nway_search(int n, const float *t, int max_evals, const NwayMeasure &m
         st = local_search(start, t0, false);
         if (st) return st;
     }
-    // 5. iterated local search with what is left of the budget: a few
-    //    random moves away from one of the three fastest plans so far (every
-    //    other restart one of them moves three or four warps between two
-    //    intervals), or -- every third restart -- three or four warps moved
-    //    in one of the packing seeds of phase 2, then first-improvement local
-    //    search.
-    // the three fastest distinct plans measured so far
-    auto elites = [&] {
+    // 5. iterated local search with what is left of the budget.  Restarts
+    //    cycle over three kinds of starting plan: one of the three fastest
+    //    plans so far; the fastest plan of one block size and register cap
+    //    (the families in turn, fastest first), so that a family that
+    //    started behind is still refined; and one of the packing seeds of
+    //    phase 2.  Every other elite or family start has three or four warps
+    //    moved between two intervals, elite and family starts then take two
+    //    or three random moves (one after a warp shift), and each restart
+    //    ends in a first-improvement local search.
+    auto by_time = [&] {
         std::vector<Seed> v = seen;
         std::sort(v.begin(), v.end(), [](const Seed &a, const Seed &b) { return a.t < b.t; });
+        return v;
+    };
+    // the three fastest distinct plans measured so far
+    auto elites = [&] {
         std::vector<NwayPlanC> e;
-        for (const Seed &sd : v) {
+        for (const Seed &sd : by_time()) {
             bool dup = false;
             for (const NwayPlanC &q : e) dup = dup || same(q, sd.p);
             if (!dup) e.push_back(sd.p);
@@ -516,21 +522,44 @@ hf_status nway_search(int n, const float *t, int max_evals, const NwayMeasure &m
         }
         return e;
     };
+    // the fastest plan of each (warps per block, register cap), fastest first
+    auto family_bests = [&] {
+        std::vector<NwayPlanC> fb;
+        for (const Seed &sd : by_time()) {
+            int w = 0;
+            for (int i = 0; i < sd.p.P; ++i) w += sd.p.warps[i];
+            bool dup = false;
+            for (const NwayPlanC &q : fb) {
+                int wq = 0;
+                for (int i = 0; i < q.P; ++i) wq += q.warps[i];
+                dup = dup || (wq == w && q.cap == sd.p.cap);
+            }
+            if (!dup) fb.push_back(sd.p);
+        }
+        return fb;
+    };
     for (int restart = 0; restart < 512 && evals + 8 < max_evals; ++restart) {
-        // start from one of the three fastest plans in turn (one lucky timing
-        // of a mediocre plan should not hold every restart), or from a
-        // packing seed, whose structure may lie far from the plans so far
-        const std::vector<NwayPlanC> el = elites();
-        const bool from_seed = restart % 3 == 2 && !seeds.empty();
-        NwayPlanC p = from_seed ? seeds[rnd(seeds.size())].p : el.empty() ? bp : el[(size_t)restart % el.size()];
-        if ((from_seed || restart % 2 == 1) && p.P > 1) {
+        const int kind = restart % 3, turn = restart / 3;
+        NwayPlanC p = bp;
+        bool shift = turn % 2 == 1;
+        if (kind == 2 && !seeds.empty()) {
+            p = seeds[rnd(seeds.size())].p;
+            shift = true;
+        } else if (kind == 1) {
+            const std::vector<NwayPlanC> fb = family_bests();
+            if (!fb.empty()) p = fb[(size_t)turn % fb.size()];
+        } else {
+            const std::vector<NwayPlanC> el = elites();
+            if (!el.empty()) p = el[(size_t)turn % el.size()];
+        }
+        if (shift && p.P > 1) {
             const int w = 3 + (int)rnd(2), i = (int)rnd(p.P), j = (i + 1 + (int)rnd(p.P - 1)) % p.P;
             if (p.warps[i] > w) {
                 p.warps[i] -= w;
                 p.warps[j] += w;
             }
         }
-        const int moves = from_seed ? 0 : 2 + (int)rnd(2) - (restart % 2);
+        const int moves = kind == 2 ? 0 : 2 + (int)rnd(2) - (shift ? 1 : 0);
         for (int m = 0; m < moves; ++m) {
             const std::vector<NwayPlanC> nb = neighbours(p);
             if (nb.empty()) break;
