@@ -444,7 +444,10 @@ typedef struct {
     int evals;
 } hf_nway_plan;
 
-/* Autotuner for N-way fusion.  Times every kernel alone (256 threads), then
+/* Autotuner for N-way fusion (an extension: the paper fuses pairs and
+ * searches their split and register bound with Algorithm 2, Sec. 3.2; the
+ * plan here also assigns several kernels to an interval).  Times every
+ * kernel alone (256 threads), then
  * packs kernels onto intervals longest-first (LPT: each goes to the least
  * loaded interval), gives each interval warps in proportion to its load, and
  * times these plans for block sizes 512, 768 and 1024, register caps
@@ -484,7 +487,8 @@ typedef float (*hf_plan_cost_fn)(const hf_nway_plan *plan, float *interval_finis
  * standalone times, `cost` is asked wherever hf_autotune_nway would time a
  * plan, trace a launch or time a finalist again.  best->evals counts the
  * plans asked for; best->grid is 0.  The library keeps nothing of `user`.
- * Returns HF_ERR_INVALID for bad arguments or when no plan has a cost. */
+ * Returns HF_ERR_INVALID for bad arguments or when no plan has a cost.  No
+ * counterpart in the paper: a test hook of the N-way extension above. */
 hf_status hf_nway_search_sim(int n, const float *standalone_us, hf_plan_cost_fn cost, void *user,
                              int max_evals, hf_nway_plan *best);
 
