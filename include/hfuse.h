@@ -451,8 +451,9 @@ typedef struct {
  * packs kernels onto intervals longest-first (LPT: each goes to the least
  * loaded interval), gives each interval warps in proportion to its load, and
  * times these plans for block sizes 512, 768 and 1024, register caps
- * none/40/48/64/96,
- * and one interval per kernel or about two kernels per interval.  Each of
+ * none/40/48/64/96, and one interval per kernel or about two kernels per
+ * interval; the packed plans also once more with warps in proportion to each
+ * interval's busiest-pipe time (from hf_body_work_of).  Each of
  * the twelve fastest is rebalanced up to six times from a traced launch
  * (hf_launch_traced), giving interval i warps in proportion to its warps
  * times its finishing time while that helps; from each of the five
@@ -469,7 +470,7 @@ typedef struct {
  * fixed-seed generator, so the search depends only on the measured
  * times).  Finally the ten fastest distinct plans are timed
  * again with 3 * reps launches and the fastest of those is returned.  The
- * seeds (at most 30) and the final timings are always done; max_evals
+ * seeds (at most 45) and the final timings are always done; max_evals
  * bounds the total including the seeds for the phases between.
  * standalone_us (n entries, may be NULL) receives the single-kernel times. */
 hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, int max_evals,

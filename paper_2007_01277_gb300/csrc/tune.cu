@@ -22,6 +22,10 @@ extern "C" {
 hf_status hf_query_single(hf_kernel k, const void *args, int threads, hf_fused_info *info);
 }
 
+namespace hf {
+int kernel_body_id(const hf_kernel_t *k);   // runtime.cu
+}
+
 // LPT plan of the N-way autotuner: kernels -> intervals, warps per interval.
 struct NwayPlanC {
     int P;
@@ -251,7 +255,10 @@ struct NwayMeasure {
 
 // The search of hf_autotune_nway over plans for n kernels whose standalone
 // times (phase 1, measured by the caller) are t[0..n): phases 2-6 below.
-hf_status nway_search(int n, const float *t, int max_evals, const NwayMeasure &m, hf_nway_plan *best)
+// issue (may be NULL) estimates each kernel's busiest-pipe time; it adds
+// seeds whose warps follow issue time instead of standalone time.
+hf_status nway_search(int n, const float *t, const float *issue, int max_evals, const NwayMeasure &m,
+                      hf_nway_plan *best)
 {
     hf_status st = HF_OK;
     int evals = 0;
@@ -293,39 +300,45 @@ hf_status nway_search(int n, const float *t, int max_evals, const NwayMeasure &m
     std::sort(order.begin(), order.end(), [&](int a, int b) { return t[a] > t[b]; });
     const int d0s[] = {512, 768, 1024};
     const int caps[] = {0, 40, 48, 64, 96};
+    double issue_tot = 0.0;
+    for (int k = 0; issue && k < n; ++k) issue_tot += std::max(0.f, issue[k]);
     for (int d0 : d0s)
         for (int cap : caps)
-            for (int P : {n, (n + 1) / 2}) {
-                const int W = d0 / 32;
-                if (P > HF_MAX_INTERVALS || P > W || P < 1) continue;
-                NwayPlanC p;
-                std::memset(&p, 0, sizeof p);
-                p.P = P;
-                p.cap = cap;
-                std::vector<double> load(P, 0.0);
-                for (int k : order) {
-                    int i = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-                    p.io[k] = i;
-                    load[i] += t[k];
+            for (int P : {n, (n + 1) / 2})
+                for (int by_issue = 0; by_issue < (issue_tot > 0.0 && P < n ? 2 : 1); ++by_issue) {
+                    const int W = d0 / 32;
+                    if (P > HF_MAX_INTERVALS || P > W || P < 1) continue;
+                    NwayPlanC p;
+                    std::memset(&p, 0, sizeof p);
+                    p.P = P;
+                    p.cap = cap;
+                    // kernels packed by standalone time; warps by standalone
+                    // or by issue time of each interval's kernels
+                    std::vector<double> load(P, 0.0), wt(P, 0.0);
+                    for (int k : order) {
+                        int i = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+                        p.io[k] = i;
+                        load[i] += t[k];
+                        wt[i] += by_issue ? std::max(0.f, issue[k]) : t[k];
+                    }
+                    double tot = 0.0;
+                    for (double l : wt) tot += l;
+                    int used = 0;
+                    for (int i = 0; i < P; ++i) {
+                        p.warps[i] = 1 + (int)((W - P) * wt[i] / tot);
+                        used += p.warps[i];
+                    }
+                    while (used < W) {   // leftover warps to the most loaded per warp
+                        int bi = 0;
+                        for (int i = 1; i < P; ++i)
+                            if (wt[i] / p.warps[i] > wt[bi] / p.warps[bi]) bi = i;
+                        ++p.warps[bi];
+                        ++used;
+                    }
+                    st = consider(p);
+                    if (st) return st;
+                    if (last_t > 0.f) seeds.push_back(Seed{last_t, last_grid, p});
                 }
-                double tot = 0.0;
-                for (double l : load) tot += l;
-                int used = 0;
-                for (int i = 0; i < P; ++i) {
-                    p.warps[i] = 1 + (int)((W - P) * load[i] / tot);
-                    used += p.warps[i];
-                }
-                while (used < W) {   // leftover warps to the most loaded per warp
-                    int bi = 0;
-                    for (int i = 1; i < P; ++i)
-                        if (load[i] / p.warps[i] > load[bi] / p.warps[bi]) bi = i;
-                    ++p.warps[bi];
-                    ++used;
-                }
-                st = consider(p);
-                if (st) return st;
-                if (last_t > 0.f) seeds.push_back(Seed{last_t, last_grid, p});
-            }
     if (best_t < 0.f) return HF_ERR_INVALID;
     std::sort(seeds.begin(), seeds.end(), [](const Seed &a, const Seed &b) { return a.t < b.t; });
     if (seeds.size() > 12) seeds.resize(12);
@@ -674,7 +687,19 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
         hf_destroy_fused(f);
         return s2;
     };
-    st = nway_search(n, t.data(), max_evals, m, best);
+    // each kernel's busiest-pipe time from its algorithmic work, at the pipe
+    // rates measured on GB300 (FFMA 3.80e13/s, 32-bit multiply 1.75e13/s,
+    // add/XOR/rotate 2.99e13/s, shared atomics 9.66e12/s); only the ratios
+    // matter: they shape the issue-weighted seeds
+    std::vector<float> issue(n, 0.f);
+    for (int k = 0; k < n; ++k) {
+        hf_body_work w;
+        if (hf_body_work_of(hf::kernel_body_id(ks[k]), args[k], &w)) continue;
+        const double us = 1e6 * std::max(std::max(w.ffma / 3.80e13, w.imul / 1.75e13),
+                                          std::max(w.ialu / 2.99e13, w.smem_atomic / 9.66e12));
+        issue[k] = (float)us;
+    }
+    st = nway_search(n, t.data(), issue.data(), max_evals, m, best);
     cudaFree(d_trace);
     return st;
 }
@@ -713,7 +738,7 @@ hf_status hf_nway_search_sim(int n, const float *standalone_us, hf_plan_cost_fn 
         int grid = 0;
         return m.time(p, us, &grid);
     };
-    return nway_search(n, standalone_us, max_evals, m, best);
+    return nway_search(n, standalone_us, nullptr, max_evals, m, best);
 }
 
 } // extern "C"
