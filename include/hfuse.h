@@ -485,13 +485,15 @@ typedef float (*hf_plan_cost_fn)(const hf_nway_plan *plan, float *interval_finis
 /* The search of hf_autotune_nway (phases after the standalone timings) run
  * against a cost function instead of the GPU, so that the search itself can
  * be tested on the host: standalone_us[0..n) stand in for the kernels'
- * standalone times, `cost` is asked wherever hf_autotune_nway would time a
- * plan, trace a launch or time a finalist again.  best->evals counts the
+ * standalone times and issue_us[0..n) (may be NULL: no issue-weighted
+ * seeds; else values >= 0) for their busiest-pipe times, and `cost` is
+ * asked wherever hf_autotune_nway would time a plan, trace a launch or time
+ * a finalist again.  best->evals counts the
  * plans asked for; best->grid is 0.  The library keeps nothing of `user`.
  * Returns HF_ERR_INVALID for bad arguments or when no plan has a cost.  No
  * counterpart in the paper: a test hook of the N-way extension above. */
-hf_status hf_nway_search_sim(int n, const float *standalone_us, hf_plan_cost_fn cost, void *user,
-                             int max_evals, hf_nway_plan *best);
+hf_status hf_nway_search_sim(int n, const float *standalone_us, const float *issue_us, hf_plan_cost_fn cost,
+                             void *user, int max_evals, hf_nway_plan *best);
 
 /* ------------------------------------------------------------------ */
 /* Source-level front-end: Algorithm 1 (Sec. 3.1) as a transformation of

@@ -704,12 +704,12 @@ hf_status hf_autotune_nway(const hf_kernel *ks, int n, const void *const *args, 
     return st;
 }
 
-hf_status hf_nway_search_sim(int n, const float *standalone_us, hf_plan_cost_fn cost, void *user,
-                             int max_evals, hf_nway_plan *best)
+hf_status hf_nway_search_sim(int n, const float *standalone_us, const float *issue_us, hf_plan_cost_fn cost,
+                             void *user, int max_evals, hf_nway_plan *best)
 {
     if (!standalone_us || !cost || !best || n < 1 || n > HF_MAX_SCHEDULE) return HF_ERR_INVALID;
     for (int k = 0; k < n; ++k)
-        if (!(standalone_us[k] > 0.f)) return HF_ERR_INVALID;
+        if (!(standalone_us[k] > 0.f) || (issue_us && !(issue_us[k] >= 0.f))) return HF_ERR_INVALID;
     auto ask = [&](const NwayPlanC &p, float *fin) -> float {
         hf_nway_plan q;
         std::memset(&q, 0, sizeof q);
@@ -738,7 +738,7 @@ hf_status hf_nway_search_sim(int n, const float *standalone_us, hf_plan_cost_fn 
         int grid = 0;
         return m.time(p, us, &grid);
     };
-    return nway_search(n, standalone_us, nullptr, max_evals, m, best);
+    return nway_search(n, standalone_us, issue_us, max_evals, m, best);
 }
 
 } // extern "C"

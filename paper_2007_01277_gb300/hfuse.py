@@ -182,8 +182,8 @@ def _load():
         "hf_bn_stats_noalloc": (_i32, [_P, _P, _P, _i32, _i32, _i32, _i32, _i32, _P]),
         "hf_autotune_nway": (_i32, [ctypes.POINTER(_P), _i32, ctypes.POINTER(_P), _i32, _i32, _i32,
                                     _P, ctypes.POINTER(NwayPlan), ctypes.POINTER(_f32)]),
-        "hf_nway_search_sim": (_i32, [_i32, ctypes.POINTER(_f32), PlanCostFn, _P, _i32,
-                                      ctypes.POINTER(NwayPlan)]),
+        "hf_nway_search_sim": (_i32, [_i32, ctypes.POINTER(_f32), ctypes.POINTER(_f32), PlanCostFn, _P,
+                                      _i32, ctypes.POINTER(NwayPlan)]),
         "hf_calibrate": (_i32, [_i32, _P, ctypes.POINTER(ctypes.c_double)]),
         "hf_src_fuse": (_i32, [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, _i32,
                                _i32, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
@@ -487,9 +487,10 @@ def hf_autotune_nway(kernels, args, max_evals=200, reps=5, flush_l2=False, strea
     return d, list(single)
 
 
-def hf_nway_search_sim(standalone_us, cost, max_evals=200):
+def hf_nway_search_sim(standalone_us, cost, max_evals=200, issue_us=None):
     """The N-way search against cost(plan_dict) -> (time, [finish per
-    interval]) instead of the GPU; returns the plan dict (with "evals")."""
+    interval]) instead of the GPU; issue_us (optional) are the kernels'
+    busiest-pipe times; returns the plan dict (with "evals")."""
     n = len(standalone_us)
 
     def cb(plan_p, fin_p, _user):
@@ -502,7 +503,8 @@ def hf_nway_search_sim(standalone_us, cost, max_evals=200):
 
     fn = PlanCostFn(cb)
     plan = NwayPlan()
-    _check("hf_nway_search_sim", lib.hf_nway_search_sim(n, (_f32 * n)(*standalone_us), fn, None,
+    iss = (_f32 * n)(*issue_us) if issue_us is not None else None
+    _check("hf_nway_search_sim", lib.hf_nway_search_sim(n, (_f32 * n)(*standalone_us), iss, fn, None,
                                                         max_evals, ctypes.byref(plan)))
     d = plan.as_dict()
     d["interval_of"] = d["interval_of"][:n]
