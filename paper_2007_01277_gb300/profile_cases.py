@@ -18,8 +18,8 @@ and prints the median CUDA-event time per launch.  Cases:
                   21*2^20 nonces fused (hits only, target 2^16)
   sha256d, blake256, blake2b  the hash scans alone (2^24, 2^25, 21*2^20)
   nway8           the eight kernels of the N-way workload in one launch with a
-                  fixed plan (--plan "io;threads;cap", default the autotuned
-                  4-interval plan)
+                  fixed plan (--plan "io;threads;cap", default an autotuned
+                  4-interval plan of one 512-thread block, no register cap)
 --scale shrinks the batch dimension (and 1-D sizes) by F for small captures.
 """
 from __future__ import annotations
@@ -128,7 +128,7 @@ def main():
     ap.add_argument("--bps", type=int, default=0)
     ap.add_argument("--threads", type=int, default=256)
     ap.add_argument("--scale", type=float, default=1.0)
-    ap.add_argument("--plan", default="2,3,2,2,1,3,0,1;384,128,288,224;64")
+    ap.add_argument("--plan", default="1,3,2,1,3,2,0,1;256,128,96,32;0")
     a = ap.parse_args()
     dev = torch.device("cuda:0")
     parts = build(a.case, a.scale, dev)
